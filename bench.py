@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: FWI fwd+adj grid-point updates per second on one GB300.
+
+One step is one pass of the whole hot path over one batch: supergather
+encoding of every posterior sample (host), the encoded misfit and velocity
+gradient of every sample over all its supergathers (forward, residual,
+adjoint, imaging; fwi_gradient), a Langevin refinement step (langevin_step)
+and a DDPM re-noise draw (renoise).  The default workload is the 2D
+thrust-belt case: 801 x 187 nodes at 25 m, 20-cell sponge, 100 sources,
+400 receivers, 8 Hz Ricker, dt 2 ms, 2000 steps, 16 posterior samples x 5
+supergathers of 20 +-1-encoded shots (80 wavefields per launch).
+
+Metric: useful updates 2 x padded points x nt x wavefields per step / time.
+Inputs (about 0.2 GB of wavefields per time step, 130 GB of snapshots per
+step) are far larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the baseline arm; it is not a GPU implementation).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "thrust2d"
+METRIC = "FWI fwd+adj Gpt/s (encoded gradient, grid-point updates/s)"
+UNIT = "Gpt/s"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def bytes_per_update(nsg):
+    """Algorithmic HBM bytes per wavefield grid-point update of each step kernel.
+
+    forward: read p^n, p^{n-1}, write p^{n+1} (12 B) + c shared by the nsg
+    supergathers of a sample (4/nsg B).  adjoint: read q^{k+1}, q^{k+2}, p^{k-1},
+    write q^k (16 B) + c and the imaging accumulator read+write shared by the
+    supergathers (12/nsg B).
+    """
+    return {"forward": 12.0 + 4.0 / nsg, "adjoint": 16.0 + 12.0 / nsg}
+
+
+def run_oracle_sample(w, nsg_sample, seed):
+    """FP64 oracle gradient for one sample over nsg_sample supergathers at full nt."""
+    import oracle as O
+    g = O.Grid.from_workload(w)
+    v = synth.initial_model(w)
+    d = synth.random_records(w, seed, nshots=w.ns)
+    perm, wt = O.encode(seed, 0, w.ns)
+    sg = w.sg_sizes[:nsg_sample]
+    t = time.perf_counter()
+    O.gradient(g, v, w.src, w.rec, d, perm, wt, sg, 1.0, scale=1.0)
+    dt = time.perf_counter() - t
+    return 2.0 * w.padded_points * w.nt * nsg_sample / dt / 1e9, dt
+
+
+def cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = synth.WORKLOADS[args.workload]()
+    nsg_sample = 1
+    for _ in range(args.warmup):
+        run_oracle_sample(w, nsg_sample, 1)
+    vals, times = [], []
+    for k in range(args.steps):
+        v, dt = run_oracle_sample(w, nsg_sample, 2 + k)
+        vals.append(v)
+        times.append(dt)
+    val = float(np.mean(vals))
+    sample = "%s: 1 sample x %d supergather of %d shots, full %d steps, fwd+adj+imaging, FP64" % (
+        w.name, nsg_sample, w.sg_sizes[0], w.nt)
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "sample": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def native_arm(args):
+    import torch
+    import paper_2512_12797_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload](**({"nt": args.nt} if args.nt else {}))
+    if args.samples:
+        w.nsamp = args.samples
+    nsamp, sg = w.nsamp, w.sg_sizes
+    nsg = len(sg)
+    B = nsamp * nsg
+    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else 0
+    ctx = P.FWI(w.grid_dict(), w.src, w.rec, B, budget)
+
+    vel0 = synth.sample_models(w, nsamp, seed=100 + rank)
+    d_obs_h = synth.random_records(w, 200 + rank)
+    vel = torch.tensor(vel0, device=dev)
+    d_obs = torch.tensor(d_obs_h, device=dev)
+    xt = torch.zeros_like(vel)
+    xprev = torch.zeros_like(vel)
+    grad = torch.empty_like(vel)
+    misfit = torch.empty(nsamp, dtype=torch.float64, device=dev)
+    sigma, eta = 1.0, 1e-3
+    beta = np.linspace(1e-4, 0.02, 1000)
+    abar = np.cumprod(1 - beta)
+    tlev = 300
+
+    def encodings(it):
+        e = [P.encode(1234 + s, it, w.ns) for s in range(nsamp)]
+        return np.stack([a for a, _ in e]), np.stack([b for _, b in e])
+
+    def step(it, vel_d, dobs_d):
+        perm, wt = encodings(it)
+        ctx.gradient(vel_d, perm, wt, sg, dobs_d, sigma, grad=grad, misfit=misfit)
+        P.langevin_step(vel_d, grad, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it)
+        P.renoise(xt, vel_d, abar[tlev - 1], abar[tlev - 2], beta[tlev - 1], 78, it, out=xprev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def timed(fn, nsteps, it0, sampler=None):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        if sampler:
+            sampler.start()
+        ev0.record()
+        for k in range(nsteps):
+            fn(it0 + k)
+        ev1.record()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1) / nsteps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms, clocks
+
+    # warm-up
+    for k in range(args.warmup):
+        step(k, vel, d_obs)
+    torch.cuda.synchronize()
+
+    # device-resident timed region, with per-phase events of the library
+    ctx.set_profiling(True)
+    phase_ms = np.zeros(4)
+    phase_launch = np.zeros(4, np.int64)
+
+    def step_prof(it):
+        step(it, vel, d_obs)
+        ms, ln = ctx.phase_times()   # synchronises on the last phase event
+        phase_ms[:] += ms
+        phase_launch[:] += ln
+
+    sampler = ClockSampler(local)
+    ms, clocks = timed(step_prof, args.steps, 1000, sampler)
+    ctx.set_profiling(False)
+    plan = ctx.plan_info()
+    units = 2.0 * w.padded_points * w.nt * B
+    value = units * world / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    vel_h = torch.tensor(vel0).pin_memory()
+    dobs_h = torch.tensor(d_obs_h).pin_memory()
+    out_h = torch.empty_like(vel_h).pin_memory()
+    mis_h = torch.empty(nsamp, dtype=torch.float64).pin_memory()
+    vel_e = torch.empty_like(vel)
+    dobs_e = torch.empty_like(d_obs)
+
+    def step_e2e(it):
+        vel_e.copy_(vel_h, non_blocking=True)
+        dobs_e.copy_(dobs_h, non_blocking=True)
+        step(it, vel_e, dobs_e)
+        out_h.copy_(vel_e, non_blocking=True)
+        mis_h.copy_(misfit, non_blocking=True)
+
+    step_e2e(0)
+    ms_e2e, _ = timed(step_e2e, max(1, args.steps), 2000)
+    e2e_value = units * world / (ms_e2e * 1e-3) / 1e9
+    h2d = vel_h.numel() * 4 + dobs_h.numel() * 4
+    d2h = out_h.numel() * 4 + nsamp * 8
+
+    # roofline of the dominant step kernel from the per-phase events
+    bpu = bytes_per_update(nsg)
+    n = args.steps
+    fwd_launch_ms = phase_ms[0] / max(phase_launch[0], 1)
+    adj_phase_launch = phase_launch[2]
+    adj_launch_ms = phase_ms[2] / max(adj_phase_launch, 1)
+    per_launch_pts = w.padded_points * B
+    kern = {
+        "step2d_kernel<ADJ>": {"ms": adj_launch_ms, "bytes": bpu["adjoint"] * per_launch_pts,
+                               "share": phase_ms[2] / max(phase_ms.sum(), 1e-9)},
+        "step2d_kernel<FWD>": {"ms": fwd_launch_ms, "bytes": bpu["forward"] * per_launch_pts,
+                               "share": phase_ms[0] / max(phase_ms.sum(), 1e-9)},
+    }
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = kern[dom]["bytes"] / (kern[dom]["ms"] * 1e-3) / 1e9
+    other = [k for k in kern if k != dom][0]
+    other_gbs = kern[other]["bytes"] / (kern[other]["ms"] * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cval, cdt = run_oracle_sample(w, 3, 3)
+        cpu = {"value": cval, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": "%s: 1 sample x 3 supergathers of %d shots, full %d steps, fwd+adj+imaging, FP64 "
+                         "(%.1f s)" % (w.name, sg[0], w.nt, cdt)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded thrust-belt models, random records)",
+           "config": {"workload": w.name, "grid": [w.nz, w.nx], "h_m": w.hx, "nb": w.nb, "nt": w.nt,
+                      "sources": w.ns, "receivers": w.nr, "samples": nsamp, "supergathers": sg,
+                      "wavefields_per_launch": B, "padded_points": w.padded_points,
+                      "parallelism": "replicas" if world > 1 else "single-gpu",
+                      "l2": "inputs larger than L2 (no flush)",
+                      "checkpoint_plan": plan},
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": ms_e2e},
+           "gpu_launches": int(phase_launch.sum() + n * 3),
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
+                        "bytes_per_update": bpu["adjoint" if "ADJ" in dom else "forward"],
+                        "avg_launch_ms": kern[dom]["ms"],
+                        "other_kernel": {"name": other, "achieved": other_gbs, "frac": other_gbs / peak,
+                                         "avg_launch_ms": kern[other]["ms"]}},
+           "phase_ms_per_step": {"forward": phase_ms[0] / n, "residual": phase_ms[1] / n,
+                                 "adjoint": phase_ms[2] / n, "finalize": phase_ms[3] / n},
+           "clocks": clocks, "cpu_baseline": cpu}
+
+    if args.checkpointed and world == 1:
+        # same step with a workspace that forces checkpointing and recompute
+        ctx.close()
+        torch.cuda.synchronize()
+        ctx2 = P.FWI(w.grid_dict(), w.src, w.rec, B, int(args.checkpointed * (1 << 30)))
+        ctx_saved = ctx2
+
+        def step_ck(it):
+            perm, wt = encodings(it)
+            ctx_saved.gradient(vel, perm, wt, sg, d_obs, sigma, grad=grad, misfit=misfit)
+            P.langevin_step(vel, grad, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it)
+            P.renoise(xt, vel, abar[tlev - 1], abar[tlev - 2], beta[tlev - 1], 78, it, out=xprev)
+
+        step_ck(0)
+        ms_ck, _ = timed(step_ck, 2, 3000)
+        out["checkpointed"] = {"value": units / (ms_ck * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_ck,
+                               "budget_gb": args.checkpointed, "plan": ctx2.plan_info()}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--budget-gb", type=float, default=0.0, help="wavefield pool (0: most of free memory)")
+    ap.add_argument("--checkpointed", type=float, default=16.0,
+                    help="also time the step with a pool of this many GB (forces recompute); 0 disables")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--samples", type=int, default=0, help="override posterior samples (profiling runs)")
+    ap.add_argument("--nt", type=int, default=0, help="override time steps (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return native_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

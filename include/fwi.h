@@ -1,0 +1,198 @@
+/*
+ * fwi.h -- C ABI of the GB300 library for the encoded simultaneous-source
+ * wave-equation likelihood gradient used by diffusion-based posterior
+ * sampling for full waveform inversion (Taufik & Alkhalifah, arXiv 2512.12797).
+ *
+ * The library computes, on one GPU, the quantities the sampler of Sec. 2.3
+ * calls at every Langevin refinement step:
+ *   - encoded predicted data  F~_j(x) = sum_{i in B_j} w_i F_i(x)        (Sec. 2.1, encoded-shot definitions)
+ *   - encoded misfit          Phi~_j  = 1/(2 sigma_y^2) ||d~_j - F~_j(x)||^2   (Sec. 2.1)
+ *   - its velocity gradient by the adjoint-state method, scaled to the
+ *     unbiased estimator (N_s/m) grad Phi~                               (Sec. 2.1, unbiased gradient)
+ *   - the Langevin refinement update                                    (Sec. 2.3 (ii))
+ *   - the DDPM re-noise draw                                            (Sec. 2.3 (iii))
+ *
+ * Discrete forward operator F_i (the paper says only that it solves the
+ * acoustic wave equation on the acquisition geometry, Sec. 2.1; this is the
+ * library's reading): constant-density damped acoustic equation
+ *     p_tt + 2 gamma p_t = v^2 (lap p + s),
+ * 8th-order central differences in space, leapfrog in time, a sponge of nb
+ * cells on every side with gamma = gmax sum_a (depth_a/nb)^2,
+ * gmax = 3 sponge_vmax ln(1/sponge_R) / (2 nb h_min), velocity edge-replicated
+ * into the sponge, zero field outside the padded grid, p^0 = p^-1 = 0,
+ *     p^{n+1} = [2 p^n - (1 - gamma dt) p^{n-1} + v^2 dt^2 (L p^n + s^n)] / (1 + gamma dt),
+ * source term s^n = sum_i w_i f(n dt) delta_{x_i} / (cell volume) with the Ricker
+ * f(t) = (1 - 2 pi^2 f0^2 (t - t0)^2) exp(-pi^2 f0^2 (t - t0)^2), records
+ * d[n][r] = p^{n+1}(x_r) for n = 0..nt-1.  The gradient is the exact gradient of
+ * this discrete misfit (discretise-then-differentiate).
+ *
+ * Conventions for every entry point
+ *   - Arrays are row-major with x fastest: physical velocity models are
+ *     [nsamp][nz][nx] (2D) or [nsamp][nz][ny][nx] (3D), float32, m/s.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory owned by the caller.  The library never
+ *     frees caller memory and keeps no caller pointer after a call returns.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Device work is
+ *     enqueued asynchronously on it; calls return once the work is enqueued.
+ *   - Return value: FWI_OK or a negative fwi_status.  Argument, geometry,
+ *     stability and allocation errors are detected on the host and returned
+ *     before anything is enqueued.  Errors found on the device (non-finite
+ *     misfit, a wait that ran out) are recorded in a per-context status word
+ *     read by fwi_last_device_status.  No C++ exception crosses this ABI.
+ *   - The library is not thread-safe per context; distinct contexts may be
+ *     used from distinct threads.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FWI_OK = 0,
+    FWI_ERR_ARG = -1,        /* invalid argument or geometry */
+    FWI_ERR_CFL = -2,        /* sponge_vmax violates the leapfrog stability bound */
+    FWI_ERR_OOM = -3,        /* device or pinned allocation failed / budget too small */
+    FWI_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+    FWI_ERR_NONFINITE = -5,  /* device status: misfit was NaN or Inf */
+    FWI_ERR_TIMEOUT = -6,    /* device status: a bounded wait ran out */
+    FWI_ERR_BOUNDS = -7      /* device status: an index check failed */
+} fwi_status;
+
+/* Physical grid, time axis, wavelet and sponge.  ny/hy are ignored in 2D. */
+typedef struct fwi_grid {
+    int ndim;                /* 2 or 3 */
+    int nz, ny, nx;          /* physical nodes (z is depth) */
+    double hz, hy, hx;       /* spacing [m] */
+    int nb;                  /* sponge cells added on every side (>= 0) */
+    double dt;               /* time step [s] */
+    int nt;                  /* time steps = samples per trace */
+    double f0, t0;           /* Ricker peak frequency [Hz] and delay [s] */
+    double sponge_vmax;      /* velocity [m/s] that sets the sponge strength; also
+                                the largest velocity the stability check admits */
+    double sponge_R;         /* target reflection coefficient in (0, 1) */
+} fwi_grid;
+
+/* Acquisition geometry: node indices (iz, iy, ix) on the physical grid, host
+ * memory, [n][3] int32 (iy ignored in 2D).  Receivers must be distinct nodes;
+ * several shots may share a node. */
+typedef struct fwi_geom {
+    int ns;
+    const int32_t* src;
+    int nr;
+    const int32_t* rec;
+} fwi_geom;
+
+typedef struct fwi_ctx fwi_ctx;
+
+/*
+ * Create a context for one grid and geometry.  The context owns all device
+ * workspace: a pool of wavefield slots (forward ring, checkpoints, snapshot
+ * buffer, adjoint ring), padded c = v^2 dt^2, gradient accumulators, receiver
+ * records.  max_wavefields bounds nsamp * nsg per call.  workspace_budget_bytes
+ * bounds the wavefield pool; 0 means "most of the free device memory".  A larger
+ * pool lets fwi_gradient keep more snapshots and recompute fewer time steps.
+ * Returns FWI_ERR_CFL if sponge_vmax^2 dt^2 * 6.5016 * sum_a 1/h_a^2 > 4
+ * (6.5016 = largest eigenvalue of the 1D 8th-order stencil, at kh = pi).
+ */
+int fwi_create(const fwi_grid* grid, const fwi_geom* geom, int max_wavefields,
+               size_t workspace_budget_bytes, fwi_ctx** out);
+void fwi_destroy(fwi_ctx* ctx);
+
+/*
+ * Supergather encoding for FWI iteration `iter` (Sec. 2.1 encoded shots; the
+ * source subsets and weights are redrawn every FWI iteration, Sec. 3.2).
+ * Host only.  Outputs perm_out[ns] (a permutation of shot ids; supergather j is
+ * the next sg_sizes[j] entries) and w_out[ns] (+1/-1 weight of shot id i).
+ * Definition (bit-exact): mix64 = SplitMix64 output function; key =
+ * mix64(seed ^ mix64(iter)); u_j = mix64(key + (j+1) * 0x9e3779b97f4a7c15);
+ * w_i = (u_i >> 63) ? -1 : +1; Fisher-Yates for i = ns-1..1 with
+ * j = (u_{ns + ns-1-i} * (i+1)) >> 64 (128-bit product), swap(perm[i], perm[j]).
+ */
+int fwi_encode(uint64_t seed, uint64_t iter, int ns, int32_t* perm_out, int8_t* w_out);
+
+/*
+ * Encoded forward modelling F~_j(x) for nsamp velocity models and nsg
+ * supergathers each (Sec. 2.1, encoded-shot definitions).
+ *   vel      device [nsamp][phys]        velocity models (m/s)
+ *   perm, w  host   [nsamp][ns]          encoding of each sample (as fwi_encode)
+ *   sg_sizes host   [nsg]                shots per supergather, sum <= ns
+ *   d_pred   device [nsamp][nsg][nt][nr] output records
+ */
+int fwi_forward(fwi_ctx* ctx, const float* vel, int nsamp, const int32_t* perm,
+                const int8_t* w, const int32_t* sg_sizes, int nsg, float* d_pred, void* stream);
+
+/*
+ * Encoded misfit and its velocity gradient (Sec. 2.1: encoded misfit,
+ * adjoint-state gradient, unbiased scaling), one forward and one adjoint solve
+ * per supergather, forward wavefields checkpointed and recomputed as the
+ * workspace allows.
+ *   d_obs    device [ns][nt][nr]   observed single-shot records d_i
+ *   sigma_y  noise standard deviation (> 0)
+ *   scale    multiplies misfit and gradient (the paper's N_s/m); <= 0 selects
+ *            N_s / sum(sg_sizes)
+ *   grad     device [nsamp][phys]  OVERWRITTEN with scale * sum_j dPhi~_j/dv
+ *   misfit   device [nsamp] double OVERWRITTEN with scale * sum_j Phi~_j
+ */
+int fwi_gradient(fwi_ctx* ctx, const float* vel, int nsamp, const int32_t* perm,
+                 const int8_t* w, const int32_t* sg_sizes, int nsg, const float* d_obs,
+                 double sigma_y, double scale, float* grad, double* misfit, void* stream);
+
+/*
+ * Clean-space Langevin refinement step (Sec. 2.3 (ii), with the independent
+ * noise scale of the modified refinement step, Sec. 2.3 closing paragraph):
+ *   z <- clamp(z - eta * grad + nu * xi, vmin, vmax)
+ * on n contiguous float32 device values; xi_i is standard normal number i of
+ * stream (seed, counter): Box-Muller on 53-bit uniforms u1 = ((a >> 11) + 1) 2^-53,
+ * u2 = (b >> 11) 2^-53 with a, b outputs 2i, 2i+1 of the SplitMix64 stream keyed
+ * mix64(seed ^ mix64(counter)).  The plain sampler uses nu = sqrt(2 eta).
+ */
+int langevin_step(float* z, const float* grad, int64_t n, double eta, double nu, double vmin,
+                  double vmax, uint64_t seed, uint64_t counter, void* stream);
+
+/*
+ * DDPM re-noise to the next level (Sec. 2.3 (iii), DDPM posterior mean and
+ * variance), elementwise on n float32 device values:
+ *   x_prev = sqrt(abar_prev) beta_t/(1-abar_t) x0 + sqrt(1-beta_t)(1-abar_prev)/(1-abar_t) x_t
+ *            + sqrt((1-abar_prev)/(1-abar_t) beta_t) xi
+ * abar_* are the paper's cumulative alpha; requires abar_t < 1 and
+ * |abar_t - abar_prev (1 - beta_t)| <= 1e-9.  xi as in langevin_step.
+ */
+int renoise(float* x_prev, const float* x_t, const float* x0, int64_t n, double abar_t,
+            double abar_prev, double beta_t, uint64_t seed, uint64_t counter, void* stream);
+
+/*
+ * Gradient of the Gaussian smoothness prior of the plain-Langevin baseline
+ *   Phi_p(z) = lam/2 sum_faces ((u_j - u_i)/h_a)^2 + mu/2 sum u_i^2,  u = z - zref,
+ * ADDED into grad (device [nsamp][phys]); zref device [phys] is shared by all samples.
+ */
+int smooth_prior_grad(fwi_ctx* ctx, const float* z, const float* zref, int nsamp, double lam,
+                      double mu, float* grad, void* stream);
+
+/* Human-readable name of a status code. */
+const char* fwi_status_string(int status);
+
+/* Synchronises `stream`, returns the device status word (FWI_OK or the first
+ * device-side error) and clears it. */
+int fwi_last_device_status(fwi_ctx* ctx, void* stream);
+
+/* Checkpoint plan of the last fwi_gradient call: snapshot segment length,
+ * number of segments, forward steps recomputed, wavefield slots used. */
+int fwi_plan_info(fwi_ctx* ctx, int* segment_len, int* nsegments, int64_t* recomputed_steps,
+                  int* slots_used, int* slots_available);
+
+/* Per-phase device timing of the last call made with profiling on (CUDA events
+ * on the call's stream): ms[0] forward, ms[1] residual+misfit, ms[2] adjoint
+ * incl. recompute, ms[3] finalize; launches[0..3] = kernel launches per phase.
+ * Synchronises on the events. */
+int fwi_set_profiling(fwi_ctx* ctx, int on);
+int fwi_phase_times(fwi_ctx* ctx, float* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FWI_H */

@@ -1,0 +1,808 @@
+// fwi_api.cu -- host side of libfwi: context, checkpoint planner, point lists,
+// TMA descriptors and the C ABI entry points declared in fwi.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "fwi_internal.cuh"
+
+using namespace fwi;
+
+// ---------------------------------------------------------------- helpers --
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return FWI_ERR_CUDA;    \
+  } while (0)
+
+constexpr double A8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+constexpr double RHO8 = 205.0 / 72.0 + 2.0 * (8.0 / 5.0 + 1.0 / 5.0 + 8.0 / 315.0 + 1.0 / 560.0);
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Checkpoint plan: snapshots p^0..p^{nt-1} are grouped in segments of K.
+// The first forward pass keeps checkpoint pairs (p^{jK-1}, p^{jK}) for the
+// segments 1..jL-1 and the snapshots of the last segment jL directly; the
+// reverse pass recomputes every other segment from its checkpoint into the
+// snapshot buffer.  Slot map: 0 zero field, 1..3 forward ring, 4..6 adjoint
+// ring, then 2 (jL-1) checkpoint slots, then K snapshot slots.
+struct Plan {
+  int nt = 0, K = 0, jL = 0;
+  long long recompute = 0;
+  int slots = 0;
+  static constexpr int ZERO = 0, RING = 1, QR = 4, CK0 = 7;
+  int seg0() const { return CK0 + 2 * std::max(jL - 1, 0); }
+  int fslot(int m) const {  // slot of p^m during the first forward pass
+    if (m <= 0) return ZERO;
+    if (m >= nt) return RING + m % 3;
+    if (m >= jL * K) return seg0() + (m - jL * K);
+    if ((m + 1) % K == 0) {
+      const int j = (m + 1) / K;
+      if (j >= 1 && j <= jL - 1) return CK0 + 2 * (j - 1);
+    }
+    if (m % K == 0) {
+      const int j = m / K;
+      if (j >= 1 && j <= jL - 1) return CK0 + 2 * (j - 1) + 1;
+    }
+    return RING + m % 3;
+  }
+  int rslot(int j, int m) const {  // slot of p^m while segment j < jL is recomputed
+    if (m == j * K - 1) return j == 0 ? ZERO : CK0 + 2 * (j - 1);
+    if (m == j * K) return j == 0 ? ZERO : CK0 + 2 * (j - 1) + 1;
+    return seg0() + (m - j * K);
+  }
+  int snap(int j, int m) const { return j == jL ? fslot(m) : rslot(j, m); }
+  int qslot(int k) const { return k > nt ? ZERO : QR + k % 3; }
+};
+
+bool make_plan(int nt, long long avail, Plan* out) {
+  bool found = false;
+  Plan best;
+  for (int K = std::min(2, nt); K <= nt; K++) {
+    Plan p;
+    p.nt = nt;
+    p.K = K;
+    p.jL = (nt + K - 1) / K - 1;
+    p.slots = Plan::CK0 + 2 * std::max(p.jL - 1, 0) + K;
+    if (p.slots > avail) continue;
+    p.recompute = (long long)p.jL * (K - 1);
+    if (!found || p.recompute < best.recompute || (p.recompute == best.recompute && p.slots < best.slots)) {
+      best = p;
+      found = true;
+    }
+  }
+  if (found) *out = best;
+  return found;
+}
+
+struct Entry {  // a point on the padded grid with a record column and amplitude
+  int z, y, x, col;
+  float amp;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- context --
+
+struct fwi_ctx {
+  fwi_grid g;
+  Layout L;
+  Coef K;
+  int ns = 0, nr = 0, max_B = 0;
+  std::vector<int> src_zyx, rec_zyx;  // padded coordinates
+  int ntx = 0, ntz = 0, nty = 1, ntiles = 0;
+  double cell_volume = 1.0, vmax_cfl = 0.0;
+
+  // device memory
+  float* pool = nullptr;
+  size_t pool_bytes = 0;
+  int pool_B = -1;  // wavefields per slot of the current partition
+  float* c = nullptr;      // [max_B][field]
+  float* G = nullptr;      // [max_B][field]
+  float* wav = nullptr;    // [nt]
+  float* dpred = nullptr;  // [max_B][nt][nr]
+  double* part = nullptr;  // [max_B][nblk]
+  float* qsrc = nullptr;   // [max_B][nt][Emax]
+  float* stmp = nullptr;   // [max_B][Emax]
+  int* status = nullptr;
+  int nblk = 0, Emax = 0;
+  // receiver lists (shared by all wavefields): forward sampling, adjoint injection
+  int* rec_off = nullptr;
+  int2* rec_smp = nullptr;
+  int4* rec_inj = nullptr;
+  // per-call lists
+  unsigned char* dlist = nullptr;
+  unsigned char* hlist = nullptr;  // pinned staging
+  size_t list_bytes = 0;
+  cudaEvent_t ev_list = nullptr;
+  // profiling
+  bool prof = false;
+  cudaEvent_t ev[5] = {};
+  long long launches[4] = {0, 0, 0, 0};
+  Plan plan;
+  long long slots_avail = 0;
+};
+
+namespace {
+
+int check_grid(const fwi_grid* g) {
+  if (!g || (g->ndim != 2 && g->ndim != 3)) return FWI_ERR_ARG;
+  if (g->nz < 1 || g->nx < 1 || (g->ndim == 3 && g->ny < 1) || g->nb < 0 || g->nt < 1) return FWI_ERR_ARG;
+  if (!(g->hz > 0) || !(g->hx > 0) || (g->ndim == 3 && !(g->hy > 0)) || !(g->dt > 0)) return FWI_ERR_ARG;
+  if (!(g->sponge_vmax > 0) || !(g->sponge_R > 0 && g->sponge_R < 1)) return FWI_ERR_ARG;
+  const double s = 1.0 / (g->hz * g->hz) + 1.0 / (g->hx * g->hx) + (g->ndim == 3 ? 1.0 / (g->hy * g->hy) : 0.0);
+  if (g->sponge_vmax * g->sponge_vmax * g->dt * g->dt * RHO8 * s > 4.0) return FWI_ERR_CFL;
+  return FWI_OK;
+}
+
+Layout make_layout(const fwi_grid* g) {
+  Layout L;
+  L.ndim = g->ndim;
+  L.nz = g->nz;
+  L.ny = g->ndim == 3 ? g->ny : 1;
+  L.nx = g->nx;
+  L.nb = g->nb;
+  L.nzp = g->nz + 2 * g->nb;
+  L.nyp = g->ndim == 3 ? g->ny + 2 * g->nb : 1;
+  L.nxp = g->nx + 2 * g->nb;
+  L.NZ = L.nzp + 2 * HALO;
+  L.NY = g->ndim == 3 ? L.nyp + 2 * HALO : 1;
+  L.SX = ((L.nxp + 2 * HALO) + 31) / 32 * 32;
+  L.field = (long long)L.NZ * L.NY * L.SX;
+  L.phys = (long long)L.nz * L.ny * L.nx;
+  return L;
+}
+
+Coef make_coef(const fwi_grid* g) {
+  Coef K;
+  for (int k = 0; k < 5; k++) {
+    K.cz[k] = (float)(A8[k] / (g->hz * g->hz));
+    K.cx[k] = (float)(A8[k] / (g->hx * g->hx));
+    K.cy[k] = g->ndim == 3 ? (float)(A8[k] / (g->hy * g->hy)) : 0.f;
+  }
+  double hmin = std::min(g->hz, g->hx);
+  if (g->ndim == 3) hmin = std::min(hmin, g->hy);
+  const double gmax = g->nb > 0 ? 3.0 * g->sponge_vmax * log(1.0 / g->sponge_R) / (2.0 * g->nb * hmin) : 0.0;
+  K.gdt = (float)(gmax * g->dt);
+  K.inv_nb = g->nb > 0 ? (float)(1.0 / g->nb) : 0.f;
+  return K;
+}
+
+// Tile of padded point (z, y, x) and its local index inside the tile.
+void tile_of(const fwi_ctx* C, const Entry& e, int* tile, int* local) {
+  const int tx = e.x / TX, tz = e.z / TZ;
+  *tile = tz * C->ntx + tx;
+  *local = (e.z % TZ) * TX + (e.x % TX);
+}
+
+// Builds CSR offsets [nb_lists][ntiles+1] and entries for lists of points.
+template <typename Fill>
+void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, int* off, Fill fill) {
+  int pos = 0;
+  for (size_t b = 0; b < lists.size(); b++) {
+    std::vector<std::pair<int, int>> order;  // (tile, index)
+    for (size_t i = 0; i < lists[b].size(); i++) {
+      int t, l;
+      tile_of(C, lists[b][i], &t, &l);
+      order.push_back({t, (int)i});
+    }
+    std::stable_sort(order.begin(), order.end());
+    size_t k = 0;
+    for (int t = 0; t <= C->ntiles; t++) {
+      off[b * (C->ntiles + 1) + t] = pos;
+      if (t == C->ntiles) break;
+      while (k < order.size() && order[k].first == t) {
+        const Entry& e = lists[b][order[k].second];
+        int tt, l;
+        tile_of(C, e, &tt, &l);
+        fill(pos, l, e);
+        pos++;
+        k++;
+      }
+    }
+  }
+}
+
+int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return FWI_ERR_CUDA;
+  const Layout& L = C->L;
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  if (L.ndim == 2) {
+    const cuuint64_t dims[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)B, (cuuint64_t)nslots};
+    const cuuint64_t str[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NZ * 4, (cuuint64_t)L.field * B * 4};
+    const cuuint32_t bh[4] = {HX, HZ, 1, 1}, bp[4] = {TX, TZ, 1, 1};
+    if (enc(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->pool, dims, str, bh, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return FWI_ERR_CUDA;
+    if (enc(plain, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->pool, dims, str, bp, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return FWI_ERR_CUDA;
+    return FWI_OK;
+  }
+  return FWI_ERR_ARG;
+}
+
+// Partition the pool into slots of B wavefields; re-zero it when the partition
+// changes so that halos and the zero slot read as zero.
+int partition_pool(fwi_ctx* C, int B, cudaStream_t st, long long* nslots) {
+  const size_t slot_bytes = (size_t)C->L.field * B * 4;
+  *nslots = (long long)(C->pool_bytes / slot_bytes);
+  if (C->pool_B != B) {
+    CK(cudaMemsetAsync(C->pool, 0, C->pool_bytes, st));
+    C->pool_B = B;
+  }
+  return FWI_OK;
+}
+
+struct CallLists {  // byte offsets into the per-call list buffer
+  size_t inj_off, inj, smp_off, smp, shot_off, shot_id, shot_w, src_cnt, src_pos, src_amp, total;
+};
+
+// Per-call lists from the encoding: merged source points per wavefield (forward
+// injection and adjoint sampling, tile CSR), shot lists for the residual, and
+// source entries for the imaging term.
+int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg, int nsg,
+                     CallLists* cl, int* Emax_out, cudaStream_t st) {
+  const int B = nsamp * nsg;
+  std::vector<std::vector<Entry>> lists(B);
+  std::vector<std::vector<std::pair<int, float>>> shots(B);
+  int Emax = 0;
+  for (int s = 0; s < nsamp; s++) {
+    int o = 0;
+    for (int j = 0; j < nsg; j++) {
+      const int b = s * nsg + j;
+      for (int k = 0; k < sg[j]; k++) {
+        const int id = perm[(long long)s * C->ns + o + k];
+        if (id < 0 || id >= C->ns) return FWI_ERR_ARG;
+        const float wt = (float)w[(long long)s * C->ns + id];
+        if (wt != 1.f && wt != -1.f) return FWI_ERR_ARG;
+        shots[b].push_back({id, wt});
+        const int z = C->src_zyx[3 * id], y = C->src_zyx[3 * id + 1], x = C->src_zyx[3 * id + 2];
+        bool merged = false;
+        for (auto& e : lists[b])
+          if (e.z == z && e.y == y && e.x == x) {
+            e.amp += wt;
+            merged = true;
+          }
+        if (!merged) lists[b].push_back({z, y, x, 0, wt});
+      }
+      o += sg[j];
+      for (size_t e = 0; e < lists[b].size(); e++) lists[b][e].col = (int)e;
+      Emax = std::max(Emax, (int)lists[b].size());
+    }
+  }
+  if (Emax > C->Emax) return FWI_ERR_ARG;
+  int nent = 0;
+  for (auto& l : lists) nent += (int)l.size();
+  int nshot = 0;
+  for (auto& l : shots) nshot += (int)l.size();
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = p;
+    p = (p + bytes + 255) / 256 * 256;
+    return r;
+  };
+  cl->inj_off = take((size_t)B * (C->ntiles + 1) * 4);
+  cl->inj = take((size_t)std::max(nent, 1) * 16);
+  cl->smp_off = take((size_t)B * (C->ntiles + 1) * 4);
+  cl->smp = take((size_t)std::max(nent, 1) * 8);
+  cl->shot_off = take((size_t)(B + 1) * 4);
+  cl->shot_id = take((size_t)std::max(nshot, 1) * 4);
+  cl->shot_w = take((size_t)std::max(nshot, 1) * 4);
+  cl->src_cnt = take((size_t)B * 4);
+  cl->src_pos = take((size_t)B * std::max(C->Emax, 1) * 8);
+  cl->src_amp = take((size_t)B * std::max(C->Emax, 1) * 4);
+  cl->total = p;
+  if (p > C->list_bytes) return FWI_ERR_ARG;
+  // the previous call's upload must have left the staging buffer
+  CK(cudaEventSynchronize(C->ev_list));
+  unsigned char* h = C->hlist;
+  const float inv_vol = (float)(1.0 / C->cell_volume);
+  build_csr(C, lists, reinterpret_cast<int*>(h + cl->inj_off), [&](int pos, int local, const Entry& e) {
+    int4 v;
+    v.x = local;
+    v.y = 0;
+    float a = e.amp * inv_vol;
+    memcpy(&v.z, &a, 4);
+    v.w = 0;
+    reinterpret_cast<int4*>(h + cl->inj)[pos] = v;
+  });
+  build_csr(C, lists, reinterpret_cast<int*>(h + cl->smp_off), [&](int pos, int local, const Entry& e) {
+    reinterpret_cast<int2*>(h + cl->smp)[pos] = make_int2(local, e.col);
+  });
+  int* so = reinterpret_cast<int*>(h + cl->shot_off);
+  int* sid = reinterpret_cast<int*>(h + cl->shot_id);
+  float* sw = reinterpret_cast<float*>(h + cl->shot_w);
+  int q = 0;
+  for (int b = 0; b < B; b++) {
+    so[b] = q;
+    for (auto& pr : shots[b]) {
+      sid[q] = pr.first;
+      sw[q] = pr.second;
+      q++;
+    }
+  }
+  so[B] = q;
+  int* cnt = reinterpret_cast<int*>(h + cl->src_cnt);
+  long long* pos = reinterpret_cast<long long*>(h + cl->src_pos);
+  float* amp = reinterpret_cast<float*>(h + cl->src_amp);
+  for (int b = 0; b < B; b++) {
+    cnt[b] = (int)lists[b].size();
+    for (size_t e = 0; e < lists[b].size(); e++) {
+      const Entry& en = lists[b][e];
+      pos[(size_t)b * C->Emax + e] = C->L.off(en.z, en.y, en.x);
+      amp[(size_t)b * C->Emax + e] = en.amp * inv_vol;
+    }
+  }
+  CK(cudaMemcpyAsync(C->dlist, C->hlist, cl->total, cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(C->ev_list, st));
+  *Emax_out = Emax;
+  return FWI_OK;
+}
+
+int validate_call(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                  int nsg) {
+  if (!C || !vel || !perm || !w || !sg || nsamp < 1 || nsg < 1) return FWI_ERR_ARG;
+  if ((long long)nsamp * nsg > C->max_B) return FWI_ERR_ARG;
+  long long tot = 0;
+  for (int j = 0; j < nsg; j++) {
+    if (sg[j] < 1) return FWI_ERR_ARG;
+    tot += sg[j];
+  }
+  if (tot > C->ns) return FWI_ERR_ARG;
+  if (C->L.ndim != 2) return FWI_ERR_ARG;  // 3D kernels not built yet
+  return FWI_OK;
+}
+
+StepParams base_params(fwi_ctx* C, int B, int nsg) {
+  StepParams P;
+  memset(&P, 0, sizeof(P));
+  P.pool = C->pool;
+  P.slot_elems = C->L.field * B;
+  P.c = C->c;
+  P.grad = C->G;
+  P.nsg = nsg;
+  P.ntx = C->ntx;
+  P.ntiles = C->ntiles;
+  P.status = C->status;
+  return P;
+}
+
+void prof_mark(fwi_ctx* C, int i, cudaStream_t st) {
+  if (C->prof) cudaEventRecord(C->ev[i], st);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- public ABI --
+
+extern "C" {
+
+const char* fwi_status_string(int s) {
+  switch (s) {
+    case FWI_OK: return "ok";
+    case FWI_ERR_ARG: return "invalid argument";
+    case FWI_ERR_CFL: return "stability (CFL) bound violated";
+    case FWI_ERR_OOM: return "out of memory";
+    case FWI_ERR_CUDA: return "CUDA error";
+    case FWI_ERR_NONFINITE: return "non-finite misfit";
+    case FWI_ERR_TIMEOUT: return "device wait timed out";
+    case FWI_ERR_BOUNDS: return "device index check failed";
+    default: return "unknown status";
+  }
+}
+
+int fwi_encode(uint64_t seed, uint64_t iter, int ns, int32_t* perm, int8_t* w) {
+  if (ns < 1 || !perm || !w) return FWI_ERR_ARG;
+  const uint64_t G = 0x9e3779b97f4a7c15ULL;
+  const uint64_t key = mix64(seed ^ mix64(iter));
+  for (int i = 0; i < ns; i++) w[i] = (mix64(key + (uint64_t)(i + 1) * G) >> 63) ? -1 : 1;
+  for (int i = 0; i < ns; i++) perm[i] = i;
+  for (int i = ns - 1; i >= 1; i--) {
+    const uint64_t u = mix64(key + ((uint64_t)ns + (uint64_t)(ns - 1 - i) + 1) * G);
+    const uint64_t j = (uint64_t)(((unsigned __int128)u * (unsigned __int128)(i + 1)) >> 64);
+    std::swap(perm[i], perm[j]);
+  }
+  return FWI_OK;
+}
+
+int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size_t budget, fwi_ctx** out) {
+  if (!out) return FWI_ERR_ARG;
+  *out = nullptr;
+  int rc = check_grid(g);
+  if (rc != FWI_OK) return rc;
+  if (!geom || geom->ns < 1 || geom->nr < 1 || !geom->src || !geom->rec || max_wavefields < 1) return FWI_ERR_ARG;
+  fwi_ctx* C = new (std::nothrow) fwi_ctx();
+  if (!C) return FWI_ERR_OOM;
+  C->g = *g;
+  C->L = make_layout(g);
+  C->K = make_coef(g);
+  C->ns = geom->ns;
+  C->nr = geom->nr;
+  C->max_B = max_wavefields;
+  C->cell_volume = g->hz * g->hx * (g->ndim == 3 ? g->hy : 1.0);
+  C->vmax_cfl = g->sponge_vmax;
+  const Layout& L = C->L;
+  auto conv = [&](const int32_t* p, int n, std::vector<int>& dst) {
+    for (int i = 0; i < n; i++) {
+      const int iz = p[3 * i], iy = g->ndim == 3 ? p[3 * i + 1] : 0, ix = p[3 * i + 2];
+      if (iz < 0 || iz >= L.nz || iy < 0 || iy >= L.ny || ix < 0 || ix >= L.nx) return false;
+      dst.push_back(iz + L.nb);
+      dst.push_back(g->ndim == 3 ? iy + L.nb : 0);
+      dst.push_back(ix + L.nb);
+    }
+    return true;
+  };
+  if (!conv(geom->src, geom->ns, C->src_zyx) || !conv(geom->rec, geom->nr, C->rec_zyx)) {
+    delete C;
+    return FWI_ERR_ARG;
+  }
+  for (int a = 0; a < C->nr; a++)
+    for (int b = a + 1; b < C->nr; b++)
+      if (C->rec_zyx[3 * a] == C->rec_zyx[3 * b] && C->rec_zyx[3 * a + 1] == C->rec_zyx[3 * b + 1] &&
+          C->rec_zyx[3 * a + 2] == C->rec_zyx[3 * b + 2]) {
+        delete C;
+        return FWI_ERR_ARG;
+      }
+  C->ntx = (L.nxp + TX - 1) / TX;
+  C->ntz = (L.nzp + TZ - 1) / TZ;
+  C->ntiles = C->ntx * C->ntz;
+  C->Emax = std::min(C->ns, 4096);
+  C->nblk = 64;
+
+  const int B = max_wavefields;
+  const size_t fbytes = (size_t)L.field * 4;
+  rc = FWI_ERR_OOM;
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max(bytes, (size_t)256)) == cudaSuccess; };
+  if (!alloc((void**)&C->c, fbytes * B) || !alloc((void**)&C->G, fbytes * B) ||
+      !alloc((void**)&C->wav, (size_t)g->nt * 4) || !alloc((void**)&C->dpred, (size_t)B * g->nt * C->nr * 4) ||
+      !alloc((void**)&C->part, (size_t)B * C->nblk * 8) ||
+      !alloc((void**)&C->qsrc, (size_t)B * g->nt * C->Emax * 4) ||
+      !alloc((void**)&C->stmp, (size_t)B * C->Emax * 4) || !alloc((void**)&C->status, 64)) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  // receiver lists, shared by every wavefield
+  {
+    std::vector<std::vector<Entry>> rl(1);
+    for (int r = 0; r < C->nr; r++) rl[0].push_back({C->rec_zyx[3 * r], C->rec_zyx[3 * r + 1], C->rec_zyx[3 * r + 2], r, 1.f});
+    std::vector<int> off(C->ntiles + 1);
+    std::vector<int2> smp(C->nr);
+    std::vector<int4> inj(C->nr);
+    build_csr(C, rl, off.data(), [&](int pos, int local, const Entry& e) {
+      smp[pos] = make_int2(local, e.col);
+      int4 v;
+      v.x = local;
+      v.y = e.col;
+      float one = 1.f;
+      memcpy(&v.z, &one, 4);
+      v.w = 0;
+      inj[pos] = v;
+    });
+    if (!alloc((void**)&C->rec_off, off.size() * 4) || !alloc((void**)&C->rec_smp, smp.size() * 8) ||
+        !alloc((void**)&C->rec_inj, inj.size() * 16)) {
+      fwi_destroy(C);
+      return FWI_ERR_OOM;
+    }
+    if (cudaMemcpy(C->rec_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C->rec_smp, smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C->rec_inj, inj.data(), inj.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+      fwi_destroy(C);
+      return FWI_ERR_CUDA;
+    }
+  }
+  // per-call list buffers (worst case: every shot its own node)
+  C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 8 + 8 + 4) +
+                  (size_t)(B + 1) * 4 + (size_t)B * C->ns * 8 + (size_t)B * 4 + 64 * 256;
+  if (!alloc((void**)&C->dlist, C->list_bytes) ||
+      cudaHostAlloc((void**)&C->hlist, C->list_bytes, cudaHostAllocDefault) != cudaSuccess) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  if (cudaEventCreateWithFlags(&C->ev_list, cudaEventDisableTiming) != cudaSuccess) {
+    fwi_destroy(C);
+    return FWI_ERR_CUDA;
+  }
+  for (int i = 0; i < 5; i++)
+    if (cudaEventCreate(&C->ev[i]) != cudaSuccess) {
+      fwi_destroy(C);
+      return FWI_ERR_CUDA;
+    }
+  // wavefield pool
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  size_t want = budget ? budget : (size_t)(0.8 * (double)fr);
+  const size_t min_pool = fbytes * B * 4;
+  if (want < min_pool || want > fr) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  C->pool_bytes = want / 256 * 256;
+  if (!alloc((void**)&C->pool, C->pool_bytes)) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  if (cudaMemset(C->status, 0, 64) != cudaSuccess || cudaMemset(C->c, 0, fbytes * B) != cudaSuccess ||
+      launch_wavelet(g->nt, g->dt, g->f0, g->t0, C->wav, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    fwi_destroy(C);
+    return FWI_ERR_CUDA;
+  }
+  *out = C;
+  return FWI_OK;
+}
+
+void fwi_destroy(fwi_ctx* C) {
+  if (!C) return;
+  cudaFree(C->pool);
+  cudaFree(C->c);
+  cudaFree(C->G);
+  cudaFree(C->wav);
+  cudaFree(C->dpred);
+  cudaFree(C->part);
+  cudaFree(C->qsrc);
+  cudaFree(C->stmp);
+  cudaFree(C->status);
+  cudaFree(C->rec_off);
+  cudaFree(C->rec_smp);
+  cudaFree(C->rec_inj);
+  cudaFree(C->dlist);
+  if (C->hlist) cudaFreeHost(C->hlist);
+  if (C->ev_list) cudaEventDestroy(C->ev_list);
+  for (int i = 0; i < 5; i++)
+    if (C->ev[i]) cudaEventDestroy(C->ev[i]);
+  delete C;
+}
+
+static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const CUtensorMap& th,
+                            const CUtensorMap& tp, const Plan* plan, float* dout, cudaStream_t st) {
+  const int B = nsamp * nsg;
+  StepParams P = base_params(C, B, nsg);
+  P.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
+  P.inj_bstride = C->ntiles + 1;
+  P.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj);
+  P.series = C->wav;
+  P.series_bstride = 0;
+  P.series_ld = 1;
+  P.smp_off = C->rec_off;
+  P.smp_bstride = 0;
+  P.smp = C->rec_smp;
+  P.smp_out = dout;
+  P.smp_bstride_out = (long long)C->g.nt * C->nr;
+  P.smp_ld = C->nr;
+  for (int n = 0; n < C->g.nt; n++) {
+    if (plan) {
+      P.s_cur = plan->fslot(n);
+      P.s_prev = plan->fslot(n - 1);
+      P.s_out = plan->fslot(n + 1);
+    } else {
+      P.s_cur = n <= 0 ? 0 : 1 + n % 3;
+      P.s_prev = n - 1 <= 0 ? 0 : 1 + (n - 1) % 3;
+      P.s_out = 1 + (n + 1) % 3;
+    }
+    P.t = n;
+    CK(launch_step2d(false, th, tp, C->L, C->K, P, nsamp, st));
+  }
+  C->launches[0] += C->g.nt;
+  return FWI_OK;
+}
+
+int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                int nsg, float* d_pred, void* stream) {
+  int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
+  if (rc != FWI_OK) return rc;
+  if (!d_pred) return FWI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = nsamp * nsg;
+  long long nslots;
+  if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
+  if (nslots < 4) return FWI_ERR_OOM;
+  CUtensorMap th, tp;
+  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp)) != FWI_OK) return rc;
+  CallLists cl;
+  int Emax;
+  if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
+  for (int i = 0; i < 4; i++) C->launches[i] = 0;
+  prof_mark(C, 0, st);
+  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->c, (float)C->vmax_cfl, C->status, st));
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, nullptr, d_pred, st)) != FWI_OK) return rc;
+  prof_mark(C, 1, st);
+  prof_mark(C, 2, st);
+  prof_mark(C, 3, st);
+  prof_mark(C, 4, st);
+  return FWI_OK;
+}
+
+int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                 int nsg, const float* d_obs, double sigma_y, double scale, float* grad, double* misfit,
+                 void* stream) {
+  int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
+  if (rc != FWI_OK) return rc;
+  if (!d_obs || !grad || !misfit || !(sigma_y > 0)) return FWI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = nsamp * nsg;
+  const int nt = C->g.nt, nr = C->nr;
+  if (!(scale > 0)) {
+    long long tot = 0;
+    for (int j = 0; j < nsg; j++) tot += sg[j];
+    scale = (double)C->ns / (double)tot;
+  }
+  long long nslots;
+  if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
+  Plan plan;
+  if (!make_plan(nt, nslots, &plan)) return FWI_ERR_OOM;
+  C->plan = plan;
+  C->slots_avail = nslots;
+  CUtensorMap th, tp;
+  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp)) != FWI_OK) return rc;
+  CallLists cl;
+  int Emax;
+  if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
+  for (int i = 0; i < 4; i++) C->launches[i] = 0;
+
+  prof_mark(C, 0, st);
+  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->c, (float)C->vmax_cfl, C->status, st));
+  CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * nsamp * 4, st));
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, &plan, C->dpred, st)) != FWI_OK) return rc;
+  prof_mark(C, 1, st);
+
+  // residual (rhat overwrites dpred) and misfit
+  const double inv_s2 = 1.0 / (sigma_y * sigma_y);
+  CK(launch_residual(B, nt, nr, C->dpred, d_obs, reinterpret_cast<const int*>(C->dlist + cl.shot_off),
+                     reinterpret_cast<const int*>(C->dlist + cl.shot_id),
+                     reinterpret_cast<const float*>(C->dlist + cl.shot_w), inv_s2, C->dpred, C->part, C->nblk, st));
+  CK(launch_misfit(nsamp, nsg, C->part, C->nblk, scale * 0.5 * inv_s2, misfit, C->status, st));
+  C->launches[1] = 2;
+  prof_mark(C, 2, st);
+
+  // reverse sweep: recompute each earlier segment, then the adjoint steps
+  StepParams F = base_params(C, B, nsg);  // recompute: sources only, no sampling
+  F.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
+  F.inj_bstride = C->ntiles + 1;
+  F.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj);
+  F.series = C->wav;
+  F.series_ld = 1;
+  StepParams A = base_params(C, B, nsg);  // adjoint: residual at receivers, sample sources
+  A.inj_off = C->rec_off;
+  A.inj_bstride = 0;
+  A.inj = C->rec_inj;
+  A.series = C->dpred;
+  A.series_bstride = (long long)nt * nr;
+  A.series_ld = nr;
+  A.smp_off = reinterpret_cast<const int*>(C->dlist + cl.smp_off);
+  A.smp_bstride = C->ntiles + 1;
+  A.smp = reinterpret_cast<const int2*>(C->dlist + cl.smp);
+  A.smp_out = C->qsrc;
+  A.smp_bstride_out = (long long)nt * C->Emax;
+  A.smp_ld = C->Emax;
+  long long adj_launch = 0;
+  for (int j = plan.jL; j >= 0; j--) {
+    const int m0 = j * plan.K, m1 = std::min((j + 1) * plan.K, nt);  // snapshots m0..m1-1
+    if (j < plan.jL) {
+      for (int n = m0; n <= m1 - 2; n++) {
+        F.s_cur = plan.rslot(j, n);
+        F.s_prev = plan.rslot(j, n - 1);
+        F.s_out = plan.rslot(j, n + 1);
+        F.t = n;
+        CK(launch_step2d(false, th, tp, C->L, C->K, F, nsamp, st));
+        adj_launch++;
+      }
+    }
+    for (int k = m1; k >= m0 + 1; k--) {
+      A.s_cur = plan.qslot(k + 1);
+      A.s_prev = plan.qslot(k + 2);
+      A.s_out = plan.qslot(k);
+      A.s_snap = plan.snap(j, k - 1);
+      A.t = k - 1;
+      CK(launch_step2d(true, th, tp, C->L, C->K, A, nsamp, st));
+      adj_launch++;
+    }
+  }
+  C->launches[2] = adj_launch;
+  prof_mark(C, 3, st);
+  CK(launch_source_imaging(B, nsg, nt, C->Emax, C->qsrc, C->wav,
+                           reinterpret_cast<const int*>(C->dlist + cl.src_cnt),
+                           reinterpret_cast<const long long*>(C->dlist + cl.src_pos),
+                           reinterpret_cast<const float*>(C->dlist + cl.src_amp), C->stmp, C->G, C->L.field, st));
+  CK(launch_finalize(C->L, vel, C->G, nsamp, scale, grad, st));
+  C->launches[3] = 3;
+  prof_mark(C, 4, st);
+  return FWI_OK;
+}
+
+int langevin_step(float* z, const float* grad, int64_t n, double eta, double nu, double vmin, double vmax,
+                  uint64_t seed, uint64_t counter, void* stream) {
+  if (!z || !grad || n < 0 || !(vmin <= vmax) || !(eta >= 0) || !(nu >= 0)) return FWI_ERR_ARG;
+  if (n == 0) return FWI_OK;
+  CK(launch_langevin(z, grad, n, eta, nu, vmin, vmax, seed, counter, (cudaStream_t)stream));
+  return FWI_OK;
+}
+
+int renoise(float* x_prev, const float* x_t, const float* x0, int64_t n, double abar_t, double abar_prev,
+            double beta_t, uint64_t seed, uint64_t counter, void* stream) {
+  if (!x_prev || !x_t || !x0 || n < 0) return FWI_ERR_ARG;
+  if (!(abar_t >= 0 && abar_t < 1) || !(abar_prev > 0 && abar_prev <= 1) || !(beta_t > 0 && beta_t < 1))
+    return FWI_ERR_ARG;
+  if (fabs(abar_t - abar_prev * (1.0 - beta_t)) > 1e-9) return FWI_ERR_ARG;
+  if (n == 0) return FWI_OK;
+  const double c0 = sqrt(abar_prev) * beta_t / (1.0 - abar_t);
+  const double ct = sqrt(1.0 - beta_t) * (1.0 - abar_prev) / (1.0 - abar_t);
+  const double sd = sqrt((1.0 - abar_prev) / (1.0 - abar_t) * beta_t);
+  CK(launch_renoise(x_prev, x_t, x0, n, c0, ct, sd, seed, counter, (cudaStream_t)stream));
+  return FWI_OK;
+}
+
+int smooth_prior_grad(fwi_ctx* C, const float* z, const float* zref, int nsamp, double lam, double mu, float* grad,
+                      void* stream) {
+  if (!C || !z || !zref || !grad || nsamp < 1 || !(lam >= 0) || !(mu >= 0)) return FWI_ERR_ARG;
+  CK(launch_prior(C->L, z, zref, nsamp, lam, mu, C->g.hz, C->g.ndim == 3 ? C->g.hy : 1.0, C->g.hx, grad,
+                  (cudaStream_t)stream));
+  return FWI_OK;
+}
+
+int fwi_last_device_status(fwi_ctx* C, void* stream) {
+  if (!C) return FWI_ERR_ARG;
+  int v = 0;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaMemcpy(&v, C->status, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemset(C->status, 0, 4));
+  return v;
+}
+
+int fwi_plan_info(fwi_ctx* C, int* K, int* nseg, int64_t* rec, int* used, int* avail) {
+  if (!C) return FWI_ERR_ARG;
+  if (K) *K = C->plan.K;
+  if (nseg) *nseg = C->plan.jL + 1;
+  if (rec) *rec = C->plan.recompute;
+  if (used) *used = C->plan.slots;
+  if (avail) *avail = (int)std::min<long long>(C->slots_avail, 1 << 30);
+  return FWI_OK;
+}
+
+int fwi_set_profiling(fwi_ctx* C, int on) {
+  if (!C) return FWI_ERR_ARG;
+  C->prof = on != 0;
+  return FWI_OK;
+}
+
+int fwi_phase_times(fwi_ctx* C, float* ms, int64_t* launches) {
+  if (!C || !C->prof) return FWI_ERR_ARG;
+  CK(cudaEventSynchronize(C->ev[4]));
+  for (int i = 0; i < 4; i++) {
+    if (ms) CK(cudaEventElapsedTime(&ms[i], C->ev[i], C->ev[i + 1]));
+    if (launches) launches[i] = C->launches[i];
+  }
+  return FWI_OK;
+}
+
+}  // extern "C"

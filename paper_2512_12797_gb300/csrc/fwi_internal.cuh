@@ -1,0 +1,176 @@
+// fwi_internal.cuh -- layout, kernel parameter blocks and sm_103a helpers
+// shared by the translation units of libfwi.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fwi.h"
+
+namespace fwi {
+
+// Wavefield storage.  Every wavefield is a padded grid (physical grid plus nb
+// sponge cells per side) surrounded by a 4-cell zero halo, so the 8th-order
+// stencil reads neighbours without bounds tests.  Row stride SX is rounded to
+// 32 floats (128 B): rows start on cache-line boundaries and every 4-column
+// group is 16-byte aligned for float4 and TMA access.
+//   element (z, y, x), padded coordinates, at ((z+4)*NY + y+4*(ndim==3))*SX + x+4
+constexpr int HALO = 4;
+constexpr int TX = 128;   // tile width (x): 32 lanes x float4
+constexpr int TZ = 32;    // tile height (z): 8 warps x 4 rows
+constexpr int RZ = 4;     // rows per thread
+constexpr int NTHREADS = 256;
+constexpr int HX = TX + 2 * HALO;   // 136
+constexpr int HZ = TZ + 2 * HALO;   // 40
+
+struct Layout {
+  int ndim;
+  int nz, ny, nx, nb;       // physical grid, sponge width
+  int nzp, nyp, nxp;        // padded grid (nyp = 1 in 2D)
+  int NZ, NY, SX;           // stored extents including the zero halo (NY = 1 in 2D)
+  long long field;          // floats per wavefield
+  long long phys;           // physical points
+  __host__ __device__ long long off(int z, int y, int x) const {
+    return ((long long)(z + HALO) * NY + (ndim == 3 ? y + HALO : 0)) * SX + (x + HALO);
+  }
+};
+
+// Stencil coefficients and sponge parameters in FP32 as the kernels use them.
+struct Coef {
+  float cz[5], cy[5], cx[5];  // a_k / h_a^2, k = 1..4 used (sum-zero form)
+  float gdt;                  // gmax * dt
+  float inv_nb;               // 1 / nb (0 when nb == 0)
+};
+
+// One time step of the forward recursion (FWD) or of the adjoint recursion
+// with the imaging condition (ADJ) over all wavefields of a call.
+struct StepParams {
+  float* pool;              // slot pool base
+  long long slot_elems;     // B * field floats per slot
+  int s_cur, s_prev, s_out, s_snap;   // slot indices
+  const float* c;           // [nsamp][field] v^2 dt^2 (padded)
+  float* grad;              // ADJ: [nsamp][field] imaging accumulator
+  int nsg;                  // wavefields per sample (b = s * nsg + j)
+  int t;                    // series / record time index
+  int ntx, ntiles;
+  // injection points per (wavefield, tile): CSR offsets inj_off[b * inj_bstride + tile]
+  const int* inj_off; int inj_bstride;
+  const int4* inj;          // {local = lz*TX + lx, col, amp (float bits), unused}
+  const float* series; long long series_bstride; int series_ld;  // amp * series[b*bs + t*ld + col]
+  // sampling points, same CSR form; smp == nullptr disables sampling
+  const int* smp_off; int smp_bstride;
+  const int2* smp;          // {local, col}
+  float* smp_out; long long smp_bstride_out; int smp_ld;
+  int* status;
+};
+
+// Host-side launchers (stencil.cu)
+cudaError_t launch_step2d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
+                          const Layout& L, const Coef& K, const StepParams& P, int nsamp,
+                          cudaStream_t st);
+cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_plane, const Layout& L, const Coef& K,
+                          const StepParams& P, int nsamp, cudaStream_t st);
+
+// Auxiliary kernels (aux.cu)
+cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, float* c,
+                          float vmax_cfl, int* status, cudaStream_t st);
+cudaError_t launch_wavelet(int nt, double dt, double f0, double t0, float* wav, cudaStream_t st);
+cudaError_t launch_residual(int B, int nt, int nr, const float* dpred, const float* dobs,
+                            const int* shot_off, const int* shot_id, const float* shot_w,
+                            double inv_sigma2, float* rhat, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_misfit(int nsamp, int nsg, const double* part, int nblk, double factor,
+                          double* misfit, int* status, cudaStream_t st);
+cudaError_t launch_source_imaging(int B, int nsg, int nt, int E, const float* qsrc,
+                                  const float* wav, const int* src_cnt, const long long* src_pos,
+                                  const float* src_amp, float* tmp, float* grad,
+                                  long long field, cudaStream_t st);
+cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp,
+                            double scale, float* grad, cudaStream_t st);
+cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, double nu,
+                            double vmin, double vmax, uint64_t seed, uint64_t counter,
+                            cudaStream_t st);
+cudaError_t launch_renoise(float* xp, const float* xt, const float* x0, long long n, double c0,
+                           double ct, double sd, uint64_t seed, uint64_t counter, cudaStream_t st);
+cudaError_t launch_prior(const Layout& L, const float* z, const float* zref, int nsamp,
+                         double lam, double mu, double hz, double hy, double hx, float* grad,
+                         cudaStream_t st);
+
+// ------------------------------------------------------------ device helpers
+
+#ifdef __CUDACC__
+// Bounded waits: a wait gives up after ~2^31 SM cycles (about a second at
+// GB300 clocks), records FWI_ERR_TIMEOUT in the status word and returns false.
+constexpr long long WAIT_CYCLES = 1LL << 31;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(status, 0, (int)FWI_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// TMA tiled loads into shared memory, completion counted on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
+// Depth into the sponge of padded index i along an axis with n physical cells.
+__device__ __forceinline__ int pad_depth(int i, int n, int nb) {
+  return i < nb ? nb - i : (i >= nb + n ? i - (nb + n - 1) : 0);
+}
+#endif
+
+}  // namespace fwi

@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative L2 <= 1e-5 on forward records and <= 1e-4 on the
+velocity gradient (FP32 device path vs FP64 oracle); +-1 encodings and
+permutations bit-exact; Gaussian draws of the sampler updates within 1e-6
+relative (FP64 on both sides, transcendental rounding only).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2512_12797_gb300 import build
+    build.build()
+    import paper_2512_12797_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def make_ctx(P, w, max_wavefields, budget=1 << 30):
+    return P.FWI(w.grid_dict(), w.src, w.rec, max_wavefields, budget)
+
+
+def test_forward_small2d_single_shot(P, torch):
+    w = synth.small2d()
+    g = O.Grid.from_workload(w)
+    v = synth.true_model(w)
+    ctx = make_ctx(P, w, 1)
+    ref = O.forward_shot(g, v, w.src[3:4], [1.0], w.rec)
+    perm = np.array([3] + [i for i in range(w.ns) if i != 3], np.int32)
+    d = ctx.forward(torch.tensor(v[None]).cuda(), perm, np.ones(w.ns, np.int8), [1])
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    e = rel(d[0, 0].cpu().numpy(), ref)
+    assert e < FWD_TOL, e
+
+
+def test_forward_small2d_encoded_supergather(P, torch):
+    w = synth.small2d()
+    g = O.Grid.from_workload(w)
+    v = synth.true_model(w)
+    perm, wt = P.encode(11, 4, w.ns)
+    ref = O.encoded_forward(g, v, w.src, w.rec, perm, wt, [8])
+    ctx = make_ctx(P, w, 1)
+    d = ctx.forward(torch.tensor(v[None]).cuda(), perm, wt, [8])
+    e = rel(d[0].cpu().numpy(), ref)
+    assert e < FWD_TOL, e
+
+
+def test_forward_linearity_on_device(P, torch):
+    # Sec. 2.1: the encoded record equals the weighted sum of single-shot records.
+    w = synth.small2d(nt=500)
+    v = torch.tensor(synth.true_model(w)[None]).cuda()
+    perm, wt = P.encode(5, 1, w.ns)
+    ctx = make_ctx(P, w, w.ns)
+    enc = ctx.forward(v, perm, wt, [w.ns])[0, 0].double()
+    single = ctx.forward(v.repeat(1, 1, 1), perm, np.ones(w.ns, np.int8), [1] * w.ns)[0].double()
+    s = sum(float(wt[perm[i]]) * single[i] for i in range(w.ns))
+    # each FP32 record is within FWD_TOL of the exact one, so their difference is too
+    e = rel(enc.cpu().numpy(), s.cpu().numpy())
+    assert e < FWD_TOL, e
+
+
+def test_gradient_small2d_matches_oracle(P, torch):
+    w = synth.small2d()
+    g = O.Grid.from_workload(w)
+    truth = synth.true_model(w)
+    v = synth.initial_model(w, truth)
+    d_obs = np.stack([O.forward_shot(g, truth, w.src[i:i + 1], [1.0], w.rec) for i in range(w.ns)])
+    perm, wt = P.encode(3, 0, w.ns)
+    sigma = 1e-3
+    phi_ref, g_ref = O.gradient(g, v, w.src, w.rec, d_obs, perm, wt, [8], sigma)
+    ctx = make_ctx(P, w, 1)
+    mis, grad = ctx.gradient(torch.tensor(v[None]).cuda(), perm, wt, [8],
+                             torch.tensor(d_obs, dtype=torch.float32).cuda(), sigma)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    e_phi = abs(mis.item() - phi_ref) / abs(phi_ref)
+    e_g = rel(grad[0].cpu().numpy(), g_ref)
+    assert e_phi < 1e-5 and e_g < GRAD_TOL, (e_phi, e_g)
+
+
+def test_gradient_batched_uneven_supergathers(P, torch):
+    # several samples with their own encodings, uneven supergathers, ragged tiles
+    w = synth.tiny2d(nz=45, nx=150, nt=250, ns=7, nr=20, nb=8)
+    g = O.Grid.from_workload(w)
+    nsamp, sg = 3, [4, 2, 1]
+    rng = np.random.default_rng(0)
+    vs = np.stack([synth.models.random_smooth_model(w.shape, 10 + s, 1500, 2500) for s in range(nsamp)])
+    d_obs = synth.random_records(w, 5)
+    encs = [P.encode(21, s, w.ns) for s in range(nsamp)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    ctx = make_ctx(P, w, nsamp * len(sg))
+    mis, grad = ctx.gradient(torch.tensor(vs).cuda(), perm, wt, sg, torch.tensor(d_obs).cuda(), 0.5)
+    torch.cuda.synchronize()
+    for s in range(nsamp):
+        phi_ref, g_ref = O.gradient(g, vs[s], w.src, w.rec, d_obs, perm[s], wt[s], sg, 0.5)
+        e_phi = abs(mis[s].item() - phi_ref) / abs(phi_ref)
+        e_g = rel(grad[s].cpu().numpy(), g_ref)
+        assert e_phi < 1e-5 and e_g < GRAD_TOL, (s, e_phi, e_g)
+
+
+def test_checkpointed_gradient_is_bit_exact(P, torch):
+    # recomputing segments from checkpoints reproduces the stored-snapshot gradient bit for bit
+    w = synth.tiny2d(nz=40, nx=70, nt=300, ns=4, nr=12, nb=6)
+    v = torch.tensor(synth.models.random_smooth_model(w.shape, 3, 1500, 2500)[None]).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 2)).cuda()
+    perm, wt = P.encode(1, 1, w.ns)
+    big = make_ctx(P, w, 2, budget=1 << 30)
+    m1, g1 = big.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    info_big = big.plan_info()
+    # a budget of 80 slots of 2 wavefields forces segments + recompute
+    field = (w.nz + 2 * w.nb + 8) * (((w.nx + 2 * w.nb + 8) + 31) // 32 * 32) * 4
+    small = make_ctx(P, w, 2, budget=80 * 2 * field)
+    m2, g2 = small.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    info_small = small.plan_info()
+    torch.cuda.synchronize()
+    assert info_big["recomputed_steps"] == 0
+    assert info_small["recomputed_steps"] > 0 and info_small["segments"] > 1
+    assert torch.equal(g1, g2) and torch.equal(m1, m2)
+
+
+def test_langevin_matches_oracle(P, torch):
+    n = 100003
+    rng = np.random.default_rng(1)
+    z = rng.uniform(1500, 3500, n).astype(np.float32)
+    gr = rng.normal(0, 1, n).astype(np.float32)
+    zt = torch.tensor(z).cuda()
+    P.langevin_step(zt, torch.tensor(gr).cuda(), 30.0, 25.0, 1500.0, 3500.0, 77, 5)
+    ref = O.langevin(z.astype(np.float64), gr.astype(np.float64), 30.0, 25.0, 1500.0, 3500.0, 77, 5)
+    got = zt.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-6
+
+
+def test_renoise_matches_oracle(P, torch):
+    beta, abar = O.ddpm_schedule()
+    t = 200
+    n = 65536
+    rng = np.random.default_rng(2)
+    xt = rng.normal(0, 1, n).astype(np.float32)
+    x0 = rng.uniform(-1, 1, n).astype(np.float32)
+    out = P.renoise(torch.tensor(xt).cuda(), torch.tensor(x0).cuda(), abar[t - 1], abar[t - 2], beta[t - 1], 9, 3)
+    ref = O.renoise(xt, x0, abar[t - 1], abar[t - 2], beta[t - 1], 9, 3)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) < 1e-6 * max(1.0, np.max(np.abs(ref)))
+    # first level: x_0 exactly
+    out1 = P.renoise(torch.tensor(xt).cuda(), torch.tensor(x0).cuda(), abar[0], 1.0, beta[0], 9, 4)
+    assert torch.equal(out1.cpu(), torch.tensor(x0))
+
+
+def test_smooth_prior_matches_oracle(P, torch):
+    w = synth.small2d()
+    g = O.Grid.from_workload(w)
+    rng = np.random.default_rng(4)
+    z = (2500 + rng.normal(0, 50, (2,) + w.shape)).astype(np.float32)
+    zr = synth.initial_model(w)
+    ctx = make_ctx(P, w, 1)
+    gr = torch.zeros(z.shape, device="cuda")
+    ctx.smooth_prior_grad(torch.tensor(z).cuda(), torch.tensor(zr).cuda(), 2.0, 0.1, gr)
+    for s in range(2):
+        _, ref = O.smooth_prior(g, z[s], zr, 2.0, 0.1)
+        assert rel(gr[s].cpu().numpy(), ref) < 1e-6
+
+
+def test_nonfinite_misfit_sets_status(P, torch):
+    w = synth.tiny2d(nt=50)
+    ctx = make_ctx(P, w, 1)
+    v = torch.tensor(synth.models.random_smooth_model(w.shape, 1, 1500, 2500)[None]).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 1)).cuda()
+    d_obs[0, 10, 3] = float("nan")
+    perm, wt = P.encode(0, 0, w.ns)
+    ctx.gradient(v, perm, wt, [w.ns], d_obs, 1.0)
+    assert ctx.device_status() == -5
+    d_obs[0, 10, 3] = 0.0
+    ctx.gradient(v, perm, wt, [w.ns], d_obs, 1.0)
+    assert ctx.device_status() == 0
+
+
+def test_velocity_above_stability_bound_sets_status(P, torch):
+    w = synth.tiny2d(nt=20)
+    ctx = make_ctx(P, w, 1)
+    v = torch.full((1,) + w.shape, 2000.0, device="cuda")
+    v[0, 5, 5] = 1e5
+    perm, wt = P.encode(0, 0, w.ns)
+    ctx.forward(v, perm, wt, [w.ns])
+    assert ctx.device_status() == -2
