@@ -173,6 +173,38 @@ int renoise(float* x_prev, const float* x_t, const float* x0, int64_t n, double 
 int smooth_prior_grad(fwi_ctx* ctx, const float* z, const float* zref, int nsamp, double lam,
                       double mu, float* grad, void* stream);
 
+/*
+ * Encoded residual and misfit for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface for users of the library.
+ * Some callers must not call cudaMalloc: code that runs while a stream is
+ * being captured (allocation is not permitted during capture), plug-ins whose
+ * host application owns the device memory pool, and latency-bound loops that
+ * cannot absorb the implicit synchronisation of an allocation.  This entry
+ * point allocates nothing and needs no context; it computes what fwi_gradient
+ * computes between its forward and adjoint passes:
+ *   rhat[b][n][r] = (d_pred[b][n][r] - sum_{i in B_b} w_i d_obs[i][n][r]) / sigma_y^2
+ *   misfit[s]     = scale * sum_j 1/(2 sigma_y^2) ||d~_j - F~_j||^2
+ *   d_pred  device [nsamp][nsg][nt][nr]   encoded predicted records (e.g. from fwi_forward)
+ *   d_obs   device [ns][nt][nr]           observed single-shot records
+ *   perm, w host [nsamp][ns], sg_sizes host [nsg]: the encoding, as in fwi_gradient
+ *   rhat    device [nsamp][nsg][nt][nr]   output (may equal d_pred: computed in place)
+ *   misfit  device [nsamp] double         output
+ *   scale   <= 0 selects N_s / sum(sg_sizes)
+ * Its scratch (FP64 partial sums, the copied encoding, shot lists) lives in
+ * one static device array of FWI_NOALLOC_MAX_BYTES that every GPU which loads
+ * the library holds until the process exits; calls whose scratch would exceed
+ * it (roughly nsamp*nsg*512 + nsamp*ns*13 bytes) return FWI_ERR_ARG.  The
+ * first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it, so make the first call
+ * on a device before any stream capture.  Every call reuses the same array,
+ * so calls that overlap on the GPU (on different streams or from different
+ * host threads) race; serialise them.  Non-finite values show up in misfit.
+ */
+#define FWI_NOALLOC_MAX_BYTES (1u << 20)
+int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_obs, int nsamp, int ns, int nt, int nr,
+                                const int32_t* perm, const int8_t* w, const int32_t* sg_sizes, int nsg,
+                                double sigma_y, double scale, float* rhat, double* misfit, void* stream);
+
 /* Human-readable name of a status code. */
 const char* fwi_status_string(int status);
 

@@ -13,7 +13,7 @@ import numpy as np
 
 from ._native import FwiError, FwiGeom, FwiGrid, check, lib, LIB_PATH, EXPORTS  # noqa: F401
 
-__all__ = ["FWI", "encode", "langevin_step", "renoise", "FwiError", "EXPORTS"]
+__all__ = ["FWI", "encode", "langevin_step", "renoise", "residual_misfit_noalloc", "FwiError", "EXPORTS"]
 
 
 def _torch():
@@ -160,3 +160,27 @@ def renoise(x_t, x0, abar_t, abar_prev, beta_t, seed, counter, out=None, stream=
                         _dev_ptr(x0, torch.float32, "x0"), x_t.numel(), float(abar_t), float(abar_prev), float(beta_t),
                         ctypes.c_uint64(seed), ctypes.c_uint64(counter), _stream(stream)), "renoise")
     return out
+
+
+def residual_misfit_noalloc(d_pred, d_obs, perm, w, sg_sizes, sigma, scale=0.0, rhat=None, misfit=None, stream=None):
+    """Encoded residual / misfit without any device allocation by the library
+    (fwi_residual_misfit_noalloc): for callers that cannot allocate.  Returns
+    (misfit [nsamp] float64, rhat like d_pred).  Calls overlapping on the GPU
+    share one static scratch array and race."""
+    torch = _torch()
+    nsamp, nsg, nt, nr = d_pred.shape
+    ns = d_obs.shape[0]
+    perm = np.ascontiguousarray(np.broadcast_to(np.asarray(perm, np.int32), (nsamp, ns)))
+    w = np.ascontiguousarray(np.broadcast_to(np.asarray(w, np.int8), (nsamp, ns)))
+    sg = np.ascontiguousarray(sg_sizes, np.int32)
+    if rhat is None:
+        rhat = torch.empty_like(d_pred)
+    if misfit is None:
+        misfit = torch.empty(nsamp, device=d_pred.device, dtype=torch.float64)
+    check(lib().fwi_residual_misfit_noalloc(
+        _dev_ptr(d_pred, torch.float32, "d_pred"), _dev_ptr(d_obs, torch.float32, "d_obs"), nsamp, ns, nt, nr,
+        perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+        sg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(sg), float(sigma), float(scale),
+        _dev_ptr(rhat, torch.float32, "rhat"), _dev_ptr(misfit, torch.float64, "misfit"), _stream(stream)),
+        "fwi_residual_misfit_noalloc")
+    return misfit, rhat

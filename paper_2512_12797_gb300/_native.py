@@ -14,7 +14,7 @@ FWI_STATUS = {0: "FWI_OK", -1: "FWI_ERR_ARG", -2: "FWI_ERR_CFL", -3: "FWI_ERR_OO
 # every symbol fwi.h declares
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradient", "langevin_step", "renoise",
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
-           "fwi_set_profiling", "fwi_phase_times"]
+           "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -61,6 +61,9 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int)]),
     "fwi_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "fwi_phase_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
+    "fwi_residual_misfit_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   _I32P, _I8P, _I32P, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_double, _P, _P, _P]),
 }
 
 
