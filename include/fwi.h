@@ -208,6 +208,10 @@ int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_obs, int nsa
 /* Human-readable name of a status code. */
 const char* fwi_status_string(int status);
 
+/* Text of the CUDA runtime error behind the most recent FWI_ERR_CUDA returned
+ * by any entry point of this library (process-wide; "no error" if none). */
+const char* fwi_last_cuda_error(void);
+
 /* Synchronises `stream`, returns the device status word (FWI_OK or the first
  * device-side error) and clears it. */
 int fwi_last_device_status(fwi_ctx* ctx, void* stream);

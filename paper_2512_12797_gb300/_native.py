@@ -14,7 +14,7 @@ FWI_STATUS = {0: "FWI_OK", -1: "FWI_ERR_ARG", -2: "FWI_ERR_CFL", -3: "FWI_ERR_OO
 # every symbol fwi.h declares
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradient", "langevin_step", "renoise",
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
-           "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc"]
+           "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -55,6 +55,7 @@ _SIGS = {
                                ctypes.c_uint64, ctypes.c_uint64, _P]),
     "smooth_prior_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P]),
     "fwi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fwi_last_cuda_error": (ctypes.c_char_p, []),
     "fwi_last_device_status": (ctypes.c_int, [_P, _P]),
     "fwi_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
@@ -84,5 +85,7 @@ def lib():
 
 def check(code, where):
     if code != 0:
+        if code == -4:
+            where = "%s [%s]" % (where, lib().fwi_last_cuda_error().decode())
         raise FwiError(code, where)
     return code

@@ -148,29 +148,30 @@ __global__ void source_dot_kernel(int nt, int E, const float* __restrict__ qsrc,
 // Adds tmp into the sample's accumulator in a fixed (supergather, entry) order.
 __global__ void source_add_kernel(int nsg, int E, const int* __restrict__ src_cnt,
                                   const long long* __restrict__ src_pos, const float* __restrict__ tmp, float* grad,
-                                  long long field) {
+                                  long long field, bool per_wavefield) {
   const int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   for (int j = 0; j < nsg; j++) {
     const int b = s * nsg + j;
-    for (int e = 0; e < src_cnt[b]; e++) grad[(long long)s * field + src_pos[(long long)b * E + e]] += tmp[(long long)b * E + e];
+    float* g = grad + (long long)(per_wavefield ? b : s) * field;
+    for (int e = 0; e < src_cnt[b]; e++) g[src_pos[(long long)b * E + e]] += tmp[(long long)b * E + e];
   }
 }
 
 cudaError_t launch_source_imaging(int B, int nsg, int nt, int E, const float* qsrc, const float* wav,
                                   const int* src_cnt, const long long* src_pos, const float* src_amp, float* tmp,
-                                  float* grad, long long field, cudaStream_t st) {
+                                  float* grad, long long field, bool per_wavefield, cudaStream_t st) {
   if (E <= 0) return cudaSuccess;
   source_dot_kernel<<<dim3((E + 7) / 8, B), 256, 0, st>>>(nt, E, qsrc, wav, src_cnt, src_amp, tmp);
-  source_add_kernel<<<B / nsg, 32, 0, st>>>(nsg, E, src_cnt, src_pos, tmp, grad, field);
+  source_add_kernel<<<B / nsg, 32, 0, st>>>(nsg, E, src_cnt, src_pos, tmp, grad, field, per_wavefield);
   return cudaGetLastError();
 }
 
 // grad_v[phys] = scale * (2 / v) * sum of G over the padded cells that replicate
 // the physical cell (adjoint of edge replication; dc/dv = 2 v dt^2 and G holds
-// c * dJ/dc).
+// c * dJ/dc), summed over the g_per_sample accumulators of each sample.
 __global__ void finalize_kernel(const Layout L, const float* __restrict__ vel, const float* __restrict__ G,
-                                int nsamp, double scale, float* grad) {
+                                int nsamp, int g_per_sample, double scale, float* grad) {
   const int ny = L.ndim == 3 ? L.ny : 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.phys * nsamp;
        i += (long long)gridDim.x * blockDim.x) {
@@ -187,20 +188,22 @@ __global__ void finalize_kernel(const Layout L, const float* __restrict__ vel, c
       y0 = iy == 0 ? 0 : iy + L.nb;
       y1 = iy == L.ny - 1 ? L.nyp - 1 : iy + L.nb;
     }
-    const float* Gs = G + (long long)s * L.field;
     double acc = 0.0;
-    for (int z = z0; z <= z1; z++)
-      for (int y = y0; y <= y1; y++)
-        for (int x = x0; x <= x1; x++) acc += Gs[L.off(z, y, x)];
+    for (int j = 0; j < g_per_sample; j++) {
+      const float* Gs = G + (long long)(s * g_per_sample + j) * L.field;
+      for (int z = z0; z <= z1; z++)
+        for (int y = y0; y <= y1; y++)
+          for (int x = x0; x <= x1; x++) acc += Gs[L.off(z, y, x)];
+    }
     grad[i] = (float)(scale * 2.0 * acc / (double)vel[i]);
   }
 }
 
-cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp, double scale,
-                            float* grad, cudaStream_t st) {
+cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp, int g_per_sample,
+                            double scale, float* grad, cudaStream_t st) {
   const long long n = L.phys * nsamp;
   const int blocks = grid_for(n, 152 * 32);
-  finalize_kernel<<<blocks, 256, 0, st>>>(L, vel, G, nsamp, scale, grad);
+  finalize_kernel<<<blocks, 256, 0, st>>>(L, vel, G, nsamp, g_per_sample, scale, grad);
   return cudaGetLastError();
 }
 

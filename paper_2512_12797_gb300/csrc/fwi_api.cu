@@ -15,10 +15,15 @@ using namespace fwi;
 
 namespace {
 
+cudaError_t g_last_cuda_error = cudaSuccess;
+
 #define CK(call)                                   \
   do {                                             \
     cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return FWI_ERR_CUDA;    \
+    if (e_ != cudaSuccess) {                       \
+      g_last_cuda_error = e_;                      \
+      return FWI_ERR_CUDA;                         \
+    }                                              \
   } while (0)
 
 constexpr double A8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
@@ -135,8 +140,9 @@ struct fwi_ctx {
   int nblk = 0, Emax = 0;
   // receiver lists (shared by all wavefields): forward sampling, adjoint injection
   int* rec_off = nullptr;
-  int2* rec_smp = nullptr;
-  int4* rec_inj = nullptr;
+  int2* rec_smp = nullptr;   // 2D sampling entries
+  int4* rec_smp4 = nullptr;  // 3D sampling entries (z in .z)
+  int4* rec_inj = nullptr;   // adjoint injection entries (z in .w)
   // per-call lists
   unsigned char* dlist = nullptr;
   unsigned char* hlist = nullptr;  // pinned staging
@@ -196,10 +202,16 @@ Coef make_coef(const fwi_grid* g) {
 }
 
 // Tile of padded point (z, y, x) and its local index inside the tile.
+// 2D tiles are 128 (x) x 32 (z); 3D tiles are 128 (x) x 8 (y) columns in z.
 void tile_of(const fwi_ctx* C, const Entry& e, int* tile, int* local) {
-  const int tx = e.x / TX, tz = e.z / TZ;
-  *tile = tz * C->ntx + tx;
-  *local = (e.z % TZ) * TX + (e.x % TX);
+  const int tx = e.x / TX;
+  if (C->L.ndim == 3) {
+    *tile = (e.y / TY3) * C->ntx + tx;
+    *local = (e.y % TY3) * TX + (e.x % TX);
+  } else {
+    *tile = (e.z / TZ) * C->ntx + tx;
+    *local = (e.z % TZ) * TX + (e.x % TX);
+  }
 }
 
 // Builds CSR offsets [nb_lists][ntiles+1] and entries for lists of points.
@@ -207,18 +219,18 @@ template <typename Fill>
 void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, int* off, Fill fill) {
   int pos = 0;
   for (size_t b = 0; b < lists.size(); b++) {
-    std::vector<std::pair<int, int>> order;  // (tile, index)
+    std::vector<std::pair<long long, int>> order;  // ((tile, z), index)
     for (size_t i = 0; i < lists[b].size(); i++) {
       int t, l;
       tile_of(C, lists[b][i], &t, &l);
-      order.push_back({t, (int)i});
+      order.push_back({(long long)t * (1LL << 32) + lists[b][i].z, (int)i});
     }
     std::stable_sort(order.begin(), order.end());
     size_t k = 0;
     for (int t = 0; t <= C->ntiles; t++) {
       off[b * (C->ntiles + 1) + t] = pos;
       if (t == C->ntiles) break;
-      while (k < order.size() && order[k].first == t) {
+      while (k < order.size() && (order[k].first >> 32) == t) {
         const Entry& e = lists[b][order[k].second];
         int tt, l;
         tile_of(C, e, &tt, &l);
@@ -249,7 +261,20 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
       return FWI_ERR_CUDA;
     return FWI_OK;
   }
-  return FWI_ERR_ARG;
+  const cuuint64_t dims[5] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)B,
+                              (cuuint64_t)nslots};
+  const cuuint64_t str[4] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4,
+                             (cuuint64_t)L.field * B * 4};
+  const cuuint32_t bh[5] = {HX, TY3 + 2 * HALO, 1, 1, 1}, bp[5] = {TX, TY3, 1, 1, 1};
+  if (enc(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, C->pool, dims, str, bh, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return FWI_ERR_CUDA;
+  if (enc(plain, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, C->pool, dims, str, bp, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return FWI_ERR_CUDA;
+  return FWI_OK;
 }
 
 // Partition the pool into slots of B wavefields; re-zero it when the partition
@@ -315,7 +340,7 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
   cl->inj_off = take((size_t)B * (C->ntiles + 1) * 4);
   cl->inj = take((size_t)std::max(nent, 1) * 16);
   cl->smp_off = take((size_t)B * (C->ntiles + 1) * 4);
-  cl->smp = take((size_t)std::max(nent, 1) * 8);
+  cl->smp = take((size_t)std::max(nent, 1) * 16);
   cl->shot_off = take((size_t)(B + 1) * 4);
   cl->shot_id = take((size_t)std::max(nshot, 1) * 4);
   cl->shot_w = take((size_t)std::max(nshot, 1) * 4);
@@ -334,11 +359,15 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
     v.y = 0;
     float a = e.amp * inv_vol;
     memcpy(&v.z, &a, 4);
-    v.w = 0;
+    v.w = e.z;
     reinterpret_cast<int4*>(h + cl->inj)[pos] = v;
   });
+  const bool is3d = C->L.ndim == 3;
   build_csr(C, lists, reinterpret_cast<int*>(h + cl->smp_off), [&](int pos, int local, const Entry& e) {
-    reinterpret_cast<int2*>(h + cl->smp)[pos] = make_int2(local, e.col);
+    if (is3d)
+      reinterpret_cast<int4*>(h + cl->smp)[pos] = make_int4(local, e.col, e.z, 0);
+    else
+      reinterpret_cast<int2*>(h + cl->smp)[pos] = make_int2(local, e.col);
   });
   int* so = reinterpret_cast<int*>(h + cl->shot_off);
   int* sid = reinterpret_cast<int*>(h + cl->shot_id);
@@ -380,7 +409,6 @@ int validate_call(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, 
     tot += sg[j];
   }
   if (tot > C->ns) return FWI_ERR_ARG;
-  if (C->L.ndim != 2) return FWI_ERR_ARG;  // 3D kernels not built yet
   return FWI_OK;
 }
 
@@ -396,6 +424,12 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
   P.ntiles = C->ntiles;
   P.status = C->status;
   return P;
+}
+
+cudaError_t launch_step(fwi_ctx* C, bool adj, const CUtensorMap& th, const CUtensorMap& tp, const StepParams& P,
+                        int nsamp, int B, cudaStream_t st) {
+  if (C->L.ndim == 3) return launch_step3d(adj, th, tp, C->L, C->K, P, B, st);
+  return launch_step2d(adj, th, tp, C->L, C->K, P, nsamp, st);
 }
 
 void prof_mark(fwi_ctx* C, int i, cudaStream_t st) {
@@ -420,6 +454,10 @@ const char* fwi_status_string(int s) {
     case FWI_ERR_BOUNDS: return "device index check failed";
     default: return "unknown status";
   }
+}
+
+const char* fwi_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no error" : cudaGetErrorString(g_last_cuda_error);
 }
 
 int fwi_encode(uint64_t seed, uint64_t iter, int ns, int32_t* perm, int8_t* w) {
@@ -476,7 +514,8 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
       }
   C->ntx = (L.nxp + TX - 1) / TX;
   C->ntz = (L.nzp + TZ - 1) / TZ;
-  C->ntiles = C->ntx * C->ntz;
+  C->nty = (L.nyp + TY3 - 1) / TY3;
+  C->ntiles = C->ntx * (g->ndim == 3 ? C->nty : C->ntz);
   C->Emax = std::min(C->ns, 4096);
   C->nblk = 64;
 
@@ -498,31 +537,34 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     for (int r = 0; r < C->nr; r++) rl[0].push_back({C->rec_zyx[3 * r], C->rec_zyx[3 * r + 1], C->rec_zyx[3 * r + 2], r, 1.f});
     std::vector<int> off(C->ntiles + 1);
     std::vector<int2> smp(C->nr);
+    std::vector<int4> smp4(C->nr);
     std::vector<int4> inj(C->nr);
     build_csr(C, rl, off.data(), [&](int pos, int local, const Entry& e) {
       smp[pos] = make_int2(local, e.col);
+      smp4[pos] = make_int4(local, e.col, e.z, 0);
       int4 v;
       v.x = local;
       v.y = e.col;
       float one = 1.f;
       memcpy(&v.z, &one, 4);
-      v.w = 0;
+      v.w = e.z;
       inj[pos] = v;
     });
     if (!alloc((void**)&C->rec_off, off.size() * 4) || !alloc((void**)&C->rec_smp, smp.size() * 8) ||
-        !alloc((void**)&C->rec_inj, inj.size() * 16)) {
+        !alloc((void**)&C->rec_smp4, smp4.size() * 16) || !alloc((void**)&C->rec_inj, inj.size() * 16)) {
       fwi_destroy(C);
       return FWI_ERR_OOM;
     }
     if (cudaMemcpy(C->rec_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(C->rec_smp, smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C->rec_smp4, smp4.data(), smp4.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(C->rec_inj, inj.data(), inj.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
       fwi_destroy(C);
       return FWI_ERR_CUDA;
     }
   }
   // per-call list buffers (worst case: every shot its own node)
-  C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 8 + 8 + 4) +
+  C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 16 + 8 + 4) +
                   (size_t)(B + 1) * 4 + (size_t)B * C->ns * 8 + (size_t)B * 4 + 64 * 256;
   if (!alloc((void**)&C->dlist, C->list_bytes) ||
       cudaHostAlloc((void**)&C->hlist, C->list_bytes, cudaHostAllocDefault) != cudaSuccess) {
@@ -575,6 +617,7 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->status);
   cudaFree(C->rec_off);
   cudaFree(C->rec_smp);
+  cudaFree(C->rec_smp4);
   cudaFree(C->rec_inj);
   cudaFree(C->dlist);
   if (C->hlist) cudaFreeHost(C->hlist);
@@ -596,7 +639,10 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
   P.series_ld = 1;
   P.smp_off = C->rec_off;
   P.smp_bstride = 0;
-  P.smp = C->rec_smp;
+  if (C->L.ndim == 3)
+    P.smp4 = C->rec_smp4;
+  else
+    P.smp = C->rec_smp;
   P.smp_out = dout;
   P.smp_bstride_out = (long long)C->g.nt * C->nr;
   P.smp_ld = C->nr;
@@ -611,7 +657,7 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
       P.s_out = 1 + (n + 1) % 3;
     }
     P.t = n;
-    CK(launch_step2d(false, th, tp, C->L, C->K, P, nsamp, st));
+    CK(launch_step(C, false, th, tp, P, nsamp, B, st));
   }
   C->launches[0] += C->g.nt;
   return FWI_OK;
@@ -672,7 +718,8 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
 
   prof_mark(C, 0, st);
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->c, (float)C->vmax_cfl, C->status, st));
-  CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * nsamp * 4, st));
+  const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
+  CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, &plan, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
@@ -701,7 +748,10 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
   A.series_ld = nr;
   A.smp_off = reinterpret_cast<const int*>(C->dlist + cl.smp_off);
   A.smp_bstride = C->ntiles + 1;
-  A.smp = reinterpret_cast<const int2*>(C->dlist + cl.smp);
+  if (C->L.ndim == 3)
+    A.smp4 = reinterpret_cast<const int4*>(C->dlist + cl.smp);
+  else
+    A.smp = reinterpret_cast<const int2*>(C->dlist + cl.smp);
   A.smp_out = C->qsrc;
   A.smp_bstride_out = (long long)nt * C->Emax;
   A.smp_ld = C->Emax;
@@ -714,7 +764,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
         F.s_prev = plan.rslot(j, n - 1);
         F.s_out = plan.rslot(j, n + 1);
         F.t = n;
-        CK(launch_step2d(false, th, tp, C->L, C->K, F, nsamp, st));
+        CK(launch_step(C, false, th, tp, F, nsamp, B, st));
         adj_launch++;
       }
     }
@@ -724,7 +774,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
       A.s_out = plan.qslot(k);
       A.s_snap = plan.snap(j, k - 1);
       A.t = k - 1;
-      CK(launch_step2d(true, th, tp, C->L, C->K, A, nsamp, st));
+      CK(launch_step(C, true, th, tp, A, nsamp, B, st));
       adj_launch++;
     }
   }
@@ -733,8 +783,9 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
   CK(launch_source_imaging(B, nsg, nt, C->Emax, C->qsrc, C->wav,
                            reinterpret_cast<const int*>(C->dlist + cl.src_cnt),
                            reinterpret_cast<const long long*>(C->dlist + cl.src_pos),
-                           reinterpret_cast<const float*>(C->dlist + cl.src_amp), C->stmp, C->G, C->L.field, st));
-  CK(launch_finalize(C->L, vel, C->G, nsamp, scale, grad, st));
+                           reinterpret_cast<const float*>(C->dlist + cl.src_amp), C->stmp, C->G, C->L.field,
+                           g_per_wf, st));
+  CK(launch_finalize(C->L, vel, C->G, nsamp, g_per_wf ? nsg : 1, scale, grad, st));
   C->launches[3] = 3;
   prof_mark(C, 4, st);
   return FWI_OK;

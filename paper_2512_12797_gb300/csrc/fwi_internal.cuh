@@ -22,6 +22,7 @@ constexpr int RZ = 4;     // rows per thread
 constexpr int NTHREADS = 256;
 constexpr int HX = TX + 2 * HALO;   // 136
 constexpr int HZ = TZ + 2 * HALO;   // 40
+constexpr int TY3 = 8;              // 3D tile height (y): 8 warps x 1 row
 
 struct Layout {
   int ndim;
@@ -59,7 +60,8 @@ struct StepParams {
   const float* series; long long series_bstride; int series_ld;  // amp * series[b*bs + t*ld + col]
   // sampling points, same CSR form; smp == nullptr disables sampling
   const int* smp_off; int smp_bstride;
-  const int2* smp;          // {local, col}
+  const int2* smp;          // {local, col}                      (2D)
+  const int4* smp4;         // {local, col, z, 0}                (3D; inj .w holds z)
   float* smp_out; long long smp_bstride_out; int smp_ld;
   int* status;
 };
@@ -68,8 +70,8 @@ struct StepParams {
 cudaError_t launch_step2d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
                           const Layout& L, const Coef& K, const StepParams& P, int nsamp,
                           cudaStream_t st);
-cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_plane, const Layout& L, const Coef& K,
-                          const StepParams& P, int nsamp, cudaStream_t st);
+cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
+                          const Layout& L, const Coef& K, const StepParams& P, int B, cudaStream_t st);
 
 // Auxiliary kernels (aux.cu)
 cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, float* c,
@@ -83,8 +85,8 @@ cudaError_t launch_misfit(int nsamp, int nsg, const double* part, int nblk, doub
 cudaError_t launch_source_imaging(int B, int nsg, int nt, int E, const float* qsrc,
                                   const float* wav, const int* src_cnt, const long long* src_pos,
                                   const float* src_amp, float* tmp, float* grad,
-                                  long long field, cudaStream_t st);
-cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp,
+                                  long long field, bool per_wavefield, cudaStream_t st);
+cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp, int g_per_sample,
                             double scale, float* grad, cudaStream_t st);
 cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, double nu,
                             double vmin, double vmax, uint64_t seed, uint64_t counter,
@@ -117,6 +119,10 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
