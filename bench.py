@@ -178,6 +178,8 @@ def native_arm(args):
     B = nsamp * nsg
     budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else 0
     ctx = P.FWI(w.grid_dict(), w.src, w.rec, B, budget)
+    if args.variants:
+        ctx.set_variants(*[int(x) for x in args.variants.split(",")])
 
     vel0 = synth.sample_models(w, nsamp, seed=100 + rank)
     d_obs_h = synth.random_records(w, 200 + rank)
@@ -246,6 +248,7 @@ def native_arm(args):
     ms, clocks = timed(step_prof, args.steps, 1000, sampler)
     ctx.set_profiling(False)
     plan = ctx.plan_info()
+    variants = ctx.variants()
     units = 2.0 * w.padded_points * w.nt * B
     value = units * world / (ms * 1e-3) / 1e9
 
@@ -305,7 +308,10 @@ def native_arm(args):
                       "wavefields_per_launch": B, "padded_points": w.padded_points,
                       "parallelism": "replicas" if world > 1 else "single-gpu",
                       "l2": "inputs larger than L2 (no flush)",
-                      "checkpoint_plan": plan},
+                      "checkpoint_plan": plan,
+                      "step_kernels": {"forward": variants["forward_name"], "adjoint": variants["adjoint_name"],
+                                       "tuner_ms_forward": variants["forward_ms"],
+                                       "tuner_ms_adjoint": variants["adjoint_ms"]}},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": ms_e2e},
            "gpu_launches": int(phase_launch.sum() + n * 3),
@@ -357,6 +363,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--samples", type=int, default=0, help="override posterior samples (profiling runs)")
     ap.add_argument("--nt", type=int, default=0, help="override time steps (profiling runs)")
+    ap.add_argument("--variants", default="", help="force step-kernel variants 'fwd,adj' (default: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

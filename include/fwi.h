@@ -221,6 +221,17 @@ int fwi_last_device_status(fwi_ctx* ctx, void* stream);
 int fwi_plan_info(fwi_ctx* ctx, int* segment_len, int* nsegments, int64_t* recomputed_steps,
                   int* slots_used, int* slots_available);
 
+/* Step-kernel variants (tile rows per thread, TMA ring depth).  By default the
+ * first fwi_forward / fwi_gradient call for a given nsamp*nsg times every
+ * compiled variant on that shape (synchronising the stream while it does)
+ * and keeps the fastest; all variants give bit-identical results.
+ * fwi_set_kernel_variants forces a variant index (-1 restores autotuning);
+ * fwi_kernel_variants reports the chosen indices and names and, in ms[0..7],
+ * the per-launch time of each variant measured by the tuner (-1: not run). */
+int fwi_set_kernel_variants(fwi_ctx* ctx, int fwd, int adj);
+int fwi_kernel_variants(fwi_ctx* ctx, int* fwd, int* adj, const char** fwd_name, const char** adj_name,
+                        float* fwd_ms, float* adj_ms, int* nvariants);
+
 /* Per-phase device timing of the last call made with profiling on (CUDA events
  * on the call's stream): ms[0] forward, ms[1] residual+misfit, ms[2] adjoint
  * incl. recompute, ms[3] finalize; launches[0..3] = kernel launches per phase.

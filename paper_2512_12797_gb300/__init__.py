@@ -129,6 +129,20 @@ class FWI:
         return {"segment_len": K.value, "segments": S.value, "recomputed_steps": rec.value,
                 "slots_used": used.value, "slots_available": avail.value}
 
+    def set_variants(self, fwd=-1, adj=-1):
+        """Force step-kernel variants (-1: autotune on the next call)."""
+        check(lib().fwi_set_kernel_variants(self._h, int(fwd), int(adj)), "fwi_set_kernel_variants")
+
+    def variants(self):
+        f, a, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        fn, an = ctypes.c_char_p(), ctypes.c_char_p()
+        fm, am = (ctypes.c_float * 8)(), (ctypes.c_float * 8)()
+        check(lib().fwi_kernel_variants(self._h, ctypes.byref(f), ctypes.byref(a), ctypes.byref(fn), ctypes.byref(an),
+                                        fm, am, ctypes.byref(n)), "fwi_kernel_variants")
+        return {"forward": f.value, "adjoint": a.value, "forward_name": (fn.value or b"").decode(),
+                "adjoint_name": (an.value or b"").decode(), "forward_ms": list(fm)[:n.value],
+                "adjoint_ms": list(am)[:n.value]}
+
     def device_status(self, stream=None):
         return lib().fwi_last_device_status(self._h, _stream(stream))
 

@@ -11,11 +11,12 @@ static inline int grid_for(long long n, int cap) { long long b = (n + 255) / 256
 
 // ------------------------------------------------------------------ setup --
 
-// c = v^2 dt^2 on the padded grid, velocity edge-replicated into the sponge.
+// cc = v^2 dt^2 / (1 + gamma dt) on the padded grid, velocity edge-replicated
+// into the sponge, gamma dt = gz[z] + gy[y] + gx[x] from the per-axis table.
 // Velocities above vmax_cfl (the stability bound checked at creation) are
 // flagged in the status word.
-__global__ void expand_kernel(const Layout L, const float* __restrict__ vel, int nsamp, double dt, float* c,
-                              float vmax_cfl, int* status) {
+__global__ void expand_kernel(const Layout L, const float* __restrict__ vel, int nsamp, double dt,
+                              const float* __restrict__ gtab, float* c, float vmax_cfl, int* status) {
   const long long npad = (long long)L.nzp * L.nyp * L.nxp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npad * nsamp;
        i += (long long)gridDim.x * blockDim.x) {
@@ -30,15 +31,16 @@ __global__ void expand_kernel(const Layout L, const float* __restrict__ vel, int
     const int py = L.ndim == 3 ? min(max(y - L.nb, 0), L.ny - 1) : 0;
     const float v = vel[(long long)s * L.phys + ((long long)pz * (L.ndim == 3 ? L.ny : 1) + py) * L.nx + px];
     if (!(v <= vmax_cfl) || !(v > 0.f)) atomicCAS(status, 0, (int)FWI_ERR_CFL);
-    c[(long long)s * L.field + L.off(z, y, x)] = (float)((double)v * (double)v * dt * dt);
+    const float g = gtab[z] + (L.ndim == 3 ? gtab[L.nzp + y] : 0.f) + gtab[L.nzp + L.nyp + x];
+    c[(long long)s * L.field + L.off(z, y, x)] = (float)((double)v * (double)v * dt * dt) * __fdividef(1.0f, 1.0f + g);
   }
 }
 
-cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, float* c, float vmax_cfl,
-                          int* status, cudaStream_t st) {
+cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, const float* gtab, float* c,
+                          float vmax_cfl, int* status, cudaStream_t st) {
   const long long n = (long long)L.nzp * L.nyp * L.nxp * nsamp;
   const int blocks = grid_for(n, 152 * 32);
-  expand_kernel<<<blocks, 256, 0, st>>>(L, vel, nsamp, dt, c, vmax_cfl, status);
+  expand_kernel<<<blocks, 256, 0, st>>>(L, vel, nsamp, dt, gtab, c, vmax_cfl, status);
   return cudaGetLastError();
 }
 

@@ -154,6 +154,13 @@ struct fwi_ctx {
   long long launches[4] = {0, 0, 0, 0};
   Plan plan;
   long long slots_avail = 0;
+  // step-kernel variants: chosen per call shape by timing (autotune), or forced
+  int var[2] = {-1, -1};
+  int forced[2] = {-1, -1};
+  int tuned_B = -1;
+  float tune_ms[2][8] = {};
+  int* zero_off = nullptr;  // [ntiles+1] zeros: "no points in any tile"
+  float* gtab = nullptr;    // gamma*dt per axis: z [nzp], y [nyp], x [nxp]
 };
 
 namespace {
@@ -242,7 +249,7 @@ void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, i
   }
 }
 
-int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain) {
+int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain, CUtensorMap* ctile) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return FWI_ERR_CUDA;
   const Layout& L = C->L;
@@ -256,6 +263,13 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return FWI_ERR_CUDA;
     if (enc(plain, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->pool, dims, str, bp, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return FWI_ERR_CUDA;
+    const cuuint64_t cd[3] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
+    const cuuint64_t cs[2] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.field * 4};
+    const cuuint32_t cb[3] = {TX, TZ, 1};
+    if (enc(ctile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C->c, cd, cs, cb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return FWI_ERR_CUDA;
@@ -274,6 +288,7 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return FWI_ERR_CUDA;
+  *ctile = *plain;  // unused by the 3D kernels
   return FWI_OK;
 }
 
@@ -418,7 +433,10 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
   P.pool = C->pool;
   P.slot_elems = C->L.field * B;
   P.c = C->c;
+  P.gtab = C->gtab;
   P.grad = C->G;
+  P.smp_off = C->zero_off;  // "no sampling points" unless a call sets a list
+  P.smp_bstride = 0;
   P.nsg = nsg;
   P.ntx = C->ntx;
   P.ntiles = C->ntiles;
@@ -426,10 +444,68 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
   return P;
 }
 
-cudaError_t launch_step(fwi_ctx* C, bool adj, const CUtensorMap& th, const CUtensorMap& tp, const StepParams& P,
-                        int nsamp, int B, cudaStream_t st) {
+cudaError_t launch_step(fwi_ctx* C, bool adj, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
+                        const StepParams& P, int nsamp, int B, cudaStream_t st) {
   if (C->L.ndim == 3) return launch_step3d(adj, th, tp, C->L, C->K, P, B, st);
-  return launch_step2d(adj, th, tp, C->L, C->K, P, nsamp, st);
+  return launch_step2d(adj, C->var[adj ? 1 : 0], th, tp, tc, C->L, C->K, P, nsamp, st);
+}
+
+// Autotuner: time every compiled variant of the forward and adjoint step
+// kernels on this call's shape (B wavefields over the real tiles, zero inputs
+// read from the zero slot, output to a ring slot, no injection or sampling)
+// and keep the fastest.  Runs once per wavefield count; synchronises the
+// stream while it times.
+int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
+             cudaStream_t st) {
+  const int B = nsamp * nsg;
+  if (C->L.ndim == 3) {
+    C->var[0] = C->var[1] = 0;
+    return FWI_OK;
+  }
+  if (C->tuned_B == B && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int adj = 0; adj < 2; adj++) {
+    const int nv = num_variants2d(adj != 0);
+    if (C->forced[adj] >= 0 && C->forced[adj] < nv) {
+      C->var[adj] = C->forced[adj];
+      continue;
+    }
+    StepParams P = base_params(C, B, nsg);
+    P.inj_off = C->zero_off;
+    P.inj_bstride = 0;
+    P.inj = C->rec_inj;
+    P.series = C->wav;
+    P.s_cur = P.s_prev = P.s_snap = Plan::ZERO;
+    P.s_out = Plan::RING;
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int v = 0; v < nv && v < 8; v++) {
+      C->tune_ms[adj][v] = -1.f;
+      if (launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st) != cudaSuccess) {
+        cudaGetLastError();  // variant does not fit this device: skip it
+        continue;
+      }
+      CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; r++) CK(launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      C->tune_ms[adj][v] = ms / 3.f;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    if (best < 0) return FWI_ERR_CUDA;
+    C->var[adj] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  C->tuned_B = B;
+  return FWI_OK;
 }
 
 void prof_mark(fwi_ctx* C, int i, cudaStream_t st) {
@@ -563,6 +639,32 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
       return FWI_ERR_CUDA;
     }
   }
+  if (!alloc((void**)&C->zero_off, (size_t)(C->ntiles + 1) * 4) ||
+      cudaMemset(C->zero_off, 0, (size_t)(C->ntiles + 1) * 4) != cudaSuccess) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  {  // per-axis gamma*dt of the sponge
+    double hmin = std::min(g->hz, g->hx);
+    if (g->ndim == 3) hmin = std::min(hmin, g->hy);
+    const double gmax = g->nb > 0 ? 3.0 * g->sponge_vmax * log(1.0 / g->sponge_R) / (2.0 * g->nb * hmin) : 0.0;
+    std::vector<float> t;
+    auto axis = [&](int n, int np) {
+      for (int i = 0; i < np; i++) {
+        const int d = i < g->nb ? g->nb - i : (i >= g->nb + n ? i - (g->nb + n - 1) : 0);
+        const double f = g->nb > 0 ? (double)d / g->nb : 0.0;
+        t.push_back((float)(gmax * g->dt * f * f));
+      }
+    };
+    axis(g->nz, L.nzp);
+    if (g->ndim == 3) axis(g->ny, L.nyp); else t.push_back(0.f);
+    axis(g->nx, L.nxp);
+    if (!alloc((void**)&C->gtab, t.size() * 4) ||
+        cudaMemcpy(C->gtab, t.data(), t.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      fwi_destroy(C);
+      return FWI_ERR_OOM;
+    }
+  }
   // per-call list buffers (worst case: every shot its own node)
   C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 16 + 8 + 4) +
                   (size_t)(B + 1) * 4 + (size_t)B * C->ns * 8 + (size_t)B * 4 + 64 * 256;
@@ -620,6 +722,8 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->rec_smp4);
   cudaFree(C->rec_inj);
   cudaFree(C->dlist);
+  cudaFree(C->zero_off);
+  cudaFree(C->gtab);
   if (C->hlist) cudaFreeHost(C->hlist);
   if (C->ev_list) cudaEventDestroy(C->ev_list);
   for (int i = 0; i < 5; i++)
@@ -628,7 +732,8 @@ void fwi_destroy(fwi_ctx* C) {
 }
 
 static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const CUtensorMap& th,
-                            const CUtensorMap& tp, const Plan* plan, float* dout, cudaStream_t st) {
+                            const CUtensorMap& tp, const CUtensorMap& tc, const Plan* plan, float* dout,
+                            cudaStream_t st) {
   const int B = nsamp * nsg;
   StepParams P = base_params(C, B, nsg);
   P.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
@@ -657,7 +762,7 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
       P.s_out = 1 + (n + 1) % 3;
     }
     P.t = n;
-    CK(launch_step(C, false, th, tp, P, nsamp, B, st));
+    CK(launch_step(C, false, th, tp, tc, P, nsamp, B, st));
   }
   C->launches[0] += C->g.nt;
   return FWI_OK;
@@ -673,15 +778,16 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   long long nslots;
   if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
   if (nslots < 4) return FWI_ERR_OOM;
-  CUtensorMap th, tp;
-  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp)) != FWI_OK) return rc;
+  CUtensorMap th, tp, tc;
+  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
+  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
   for (int i = 0; i < 4; i++) C->launches[i] = 0;
   prof_mark(C, 0, st);
-  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->c, (float)C->vmax_cfl, C->status, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, nullptr, d_pred, st)) != FWI_OK) return rc;
+  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, nullptr, d_pred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
   prof_mark(C, 2, st);
   prof_mark(C, 3, st);
@@ -709,18 +815,19 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
   if (!make_plan(nt, nslots, &plan)) return FWI_ERR_OOM;
   C->plan = plan;
   C->slots_avail = nslots;
-  CUtensorMap th, tp;
-  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp)) != FWI_OK) return rc;
+  CUtensorMap th, tp, tc;
+  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
+  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
   for (int i = 0; i < 4; i++) C->launches[i] = 0;
 
   prof_mark(C, 0, st);
-  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->c, (float)C->vmax_cfl, C->status, st));
+  CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
   const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
   CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, &plan, C->dpred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, &plan, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
   // residual (rhat overwrites dpred) and misfit
@@ -764,7 +871,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
         F.s_prev = plan.rslot(j, n - 1);
         F.s_out = plan.rslot(j, n + 1);
         F.t = n;
-        CK(launch_step(C, false, th, tp, F, nsamp, B, st));
+        CK(launch_step(C, false, th, tp, tc, F, nsamp, B, st));
         adj_launch++;
       }
     }
@@ -774,7 +881,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
       A.s_out = plan.qslot(k);
       A.s_snap = plan.snap(j, k - 1);
       A.t = k - 1;
-      CK(launch_step(C, true, th, tp, A, nsamp, B, st));
+      CK(launch_step(C, true, th, tp, tc, A, nsamp, B, st));
       adj_launch++;
     }
   }
@@ -837,6 +944,32 @@ int fwi_plan_info(fwi_ctx* C, int* K, int* nseg, int64_t* rec, int* used, int* a
   if (rec) *rec = C->plan.recompute;
   if (used) *used = C->plan.slots;
   if (avail) *avail = (int)std::min<long long>(C->slots_avail, 1 << 30);
+  return FWI_OK;
+}
+
+int fwi_set_kernel_variants(fwi_ctx* C, int fwd, int adj) {
+  if (!C) return FWI_ERR_ARG;
+  if (C->L.ndim == 2 && (fwd >= num_variants2d(false) || adj >= num_variants2d(true))) return FWI_ERR_ARG;
+  C->forced[0] = fwd < 0 ? -1 : fwd;
+  C->forced[1] = adj < 0 ? -1 : adj;
+  C->tuned_B = -1;
+  return FWI_OK;
+}
+
+int fwi_kernel_variants(fwi_ctx* C, int* fwd, int* adj, const char** fwd_name, const char** adj_name,
+                        float* fwd_ms, float* adj_ms, int* nvariants) {
+  if (!C) return FWI_ERR_ARG;
+  const bool d2 = C->L.ndim == 2;
+  if (fwd) *fwd = C->var[0];
+  if (adj) *adj = C->var[1];
+  if (fwd_name) *fwd_name = d2 ? variant2d_name(false, C->var[0]) : "fwd3d";
+  if (adj_name) *adj_name = d2 ? variant2d_name(true, C->var[1]) : "adj3d";
+  const int n = d2 ? std::max(num_variants2d(false), num_variants2d(true)) : 1;
+  if (nvariants) *nvariants = n;
+  for (int v = 0; v < n && v < 8; v++) {
+    if (fwd_ms) fwd_ms[v] = C->tune_ms[0][v];
+    if (adj_ms) adj_ms[v] = C->tune_ms[1][v];
+  }
   return FWI_OK;
 }
 

@@ -49,7 +49,8 @@ struct StepParams {
   float* pool;              // slot pool base
   long long slot_elems;     // B * field floats per slot
   int s_cur, s_prev, s_out, s_snap;   // slot indices
-  const float* c;           // [nsamp][field] v^2 dt^2 (padded)
+  const float* c;           // [nsamp][field] cc = v^2 dt^2 / (1 + gamma dt) (padded)
+  const float* gtab;        // gamma*dt per axis: z [nzp], then y [nyp], then x [nxp]
   float* grad;              // ADJ: [nsamp][field] imaging accumulator
   int nsg;                  // wavefields per sample (b = s * nsg + j)
   int t;                    // series / record time index
@@ -67,14 +68,16 @@ struct StepParams {
 };
 
 // Host-side launchers (stencil.cu)
-cudaError_t launch_step2d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
-                          const Layout& L, const Coef& K, const StepParams& P, int nsamp,
+cudaError_t launch_step2d(bool adj, int variant, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
+                          const CUtensorMap& tm_c, const Layout& L, const Coef& K, const StepParams& P, int nsamp,
                           cudaStream_t st);
+int num_variants2d(bool adj);
+const char* variant2d_name(bool adj, int v);
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
                           const Layout& L, const Coef& K, const StepParams& P, int B, cudaStream_t st);
 
 // Auxiliary kernels (aux.cu)
-cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, float* c,
+cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, const float* gtab, float* c,
                           float vmax_cfl, int* status, cudaStream_t st);
 cudaError_t launch_wavelet(int nt, double dt, double f0, double t0, float* wav, cudaStream_t st);
 cudaError_t launch_residual(int B, int nt, int nr, const float* dpred, const float* dobs,
@@ -159,6 +162,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             int c3, int c4, uint64_t* bar) {
   asm volatile(
@@ -168,6 +180,18 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* tm, in
       "r"(smem_u32(bar))
       : "memory");
 }
+
+// 4-byte asynchronous global->shared copies whose completion is counted as
+// one (non-incrementing) arrival on an mbarrier.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Sponge coefficient b = (1 - g)/(1 + g) from g = gamma*dt (fast reciprocal).
+__device__ __forceinline__ float sponge_b(float g) { return (1.0f - g) * __fdividef(1.0f, 1.0f + g); }
 
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* tm) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");

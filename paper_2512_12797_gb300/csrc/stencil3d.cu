@@ -1,6 +1,8 @@
 // stencil3d.cu -- 3D time-step kernels (forward recursion; adjoint recursion
 // with the imaging condition), same algebra as the 2D kernels in stencil.cu:
 //     p^{n+1} = p^n + b (p^n - p^{n-1}) + cc (L p^n + s^n),  L = sum_a sum_k a_k/h_a^2 [(p_{+k} + p_{-k}) - 2p]
+// (cc = v^2 dt^2/(1 + gamma dt) is read from the expanded array; b = (1 - gamma dt)/(1 + gamma dt)
+// from the per-axis gamma*dt table)
 //     q^k     = q^{k+1} + b (q^{k+1} - q^{k+2}) + cc (L q^{k+1} + R^T rhat^{k-1}),  G += q^k L p^{k-1}.
 //
 // 2.5D blocking: a CTA owns a 128 (x) x 8 (y) column of one wavefield and
@@ -70,15 +72,6 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   }
 }
 
-__device__ __forceinline__ void sponge3d(const Layout& L, const Coef& K, int z, int y, int x, float& b, float& inv) {
-  const float dz = pad_depth(z, L.nz, L.nb) * K.inv_nb;
-  const float dy = pad_depth(y, L.ny, L.nb) * K.inv_nb;
-  const float dx = pad_depth(x, L.nx, L.nb) * K.inv_nb;
-  const float gdt = K.gdt * (dz * dz + dy * dy + dx * dx);
-  inv = __frcp_rn(1.0f + gdt);
-  b = (1.0f - gdt) * inv;
-}
-
 template <bool ADJ>
 __global__ void __launch_bounds__(NTHREADS, 1)
 step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
@@ -135,6 +128,12 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   float* outp = P.pool + (long long)P.s_out * P.slot_elems + (long long)b * L.field;
   float* gb = ADJ ? P.grad + (long long)b * L.field : nullptr;
 
+  // sponge table entries of this thread's y row and x columns
+  const float gyv = gy < L.nyp ? __ldg(P.gtab + L.nzp + gy) : 0.f;
+  float gxv[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) gxv[j] = gx + j < L.nxp ? __ldg(P.gtab + L.nzp + L.nyp + gx + j) : 0.f;
+
   float4 Q[9], QS[9];
 #pragma unroll
   for (int i = 0; i < 9; i++) {
@@ -163,13 +162,13 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
       const float4 pm = ld4s(s_prev + slot * PPLANE + ly * TX + lx);
       float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
       if (colv) cv = __ldg(reinterpret_cast<const float4*>(cs + L.off(z, gy, gx)));
+      const float gzy = __ldg(P.gtab + z) + gyv;
       float nv[4];
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        float bb, inv;
-        sponge3d(L, K, z, gy, gx + j, bb, inv);
+        const float bb = sponge_b(gzy + gxv[j]);
         const float p = comp(Q[4], j);
-        nv[j] = fmaf(comp(cv, j) * inv, lap[j], fmaf(bb, p - comp(pm, j), p));
+        nv[j] = fmaf(comp(cv, j), lap[j], fmaf(bb, p - comp(pm, j), p));
       }
       // injection / sampling at this level (only tiles with points at level z)
       bool mine = false;
@@ -182,9 +181,7 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
           const int4 en = P.inj[e];
           if (en.w != z) continue;
           const int yy = y0 + en.x / TX, xx = x0 + en.x % TX;
-          float bb, inv;
-          sponge3d(L, K, z, yy, xx, bb, inv);
-          const float ccp = __ldg(cs + L.off(z, yy, xx)) * inv;
+          const float ccp = __ldg(cs + L.off(z, yy, xx));
           s_stage[en.x] += ccp * (__int_as_float(en.z) *
                                   P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
         }

@@ -206,3 +206,29 @@ def test_velocity_above_stability_bound_sets_status(P, torch):
     perm, wt = P.encode(0, 0, w.ns)
     ctx.forward(v, perm, wt, [w.ns])
     assert ctx.device_status() == -2
+
+
+def test_all_step_kernel_variants_bit_identical(P, torch):
+    # every compiled tile/ring variant performs the same per-point arithmetic
+    w = synth.tiny2d(nz=50, nx=300, nt=120, ns=6, nr=30, nb=10)
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 40 + s, 1500, 2500)
+                               for s in range(2)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 4)).cuda()
+    perm, wt = P.encode(8, 1, w.ns)
+    ctx = make_ctx(P, w, 6)
+    ref = None
+    nvar = len(ctx.variants()["forward_ms"])
+    for fv in range(nvar):
+        ctx.set_variants(fv, fv % 4)
+        m, g = ctx.gradient(v, perm, wt, [3, 2, 1], d_obs, 1.0)
+        info = ctx.variants()
+        assert info["forward"] == fv and info["adjoint"] == fv % 4
+        if ref is None:
+            ref = (m.clone(), g.clone())
+        else:
+            assert torch.equal(m, ref[0]) and torch.equal(g, ref[1]), info
+    ctx.set_variants(-1, -1)
+    m, g = ctx.gradient(v, perm, wt, [3, 2, 1], d_obs, 1.0)
+    info = ctx.variants()
+    assert min(x for x in info["forward_ms"] if x > 0) > 0
+    assert torch.equal(g, ref[1])
