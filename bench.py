@@ -103,14 +103,17 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def bytes_per_update(nsg):
+def bytes_per_update(nsg, ndim=2):
     """Algorithmic HBM bytes per wavefield grid-point update of each step kernel.
 
-    forward: read p^n, p^{n-1}, write p^{n+1} (12 B) + c shared by the nsg
-    supergathers of a sample (4/nsg B).  adjoint: read q^{k+1}, q^{k+2}, p^{k-1},
-    write q^k (16 B) + c and the imaging accumulator read+write shared by the
-    supergathers (12/nsg B).
+    2D forward: read p^n, p^{n-1}, write p^{n+1} (12 B) + cc shared by the nsg
+    supergathers of a sample (4/nsg B).  2D adjoint: read q^{k+1}, q^{k+2},
+    p^{k-1}, write q^k (16 B) + cc and the imaging accumulator read+write
+    shared by the supergathers (12/nsg B).  3D kernels own one wavefield per
+    CTA: forward 16 B, adjoint 16 B + cc 4 B + accumulator read+write 8 B.
     """
+    if ndim == 3:
+        return {"forward": 16.0, "adjoint": 28.0}
     return {"forward": 12.0 + 4.0 / nsg, "adjoint": 16.0 + 12.0 / nsg}
 
 
@@ -274,17 +277,24 @@ def native_arm(args):
     d2h = out_h.numel() * 4 + nsamp * 8
 
     # roofline of the dominant step kernel from the per-phase events
-    bpu = bytes_per_update(nsg)
+    bpu = bytes_per_update(nsg, w.ndim)
     n = args.steps
-    fwd_launch_ms = phase_ms[0] / max(phase_launch[0], 1)
+    nchunks = (nsamp + plan["samples_per_chunk"] - 1) // plan["samples_per_chunk"]
+    fwd_launch_ms = phase_ms[0] / max(phase_launch[0] - nchunks * n, 1)  # phase 0 also holds one expand per chunk
     adj_phase_launch = phase_launch[2]
     adj_launch_ms = phase_ms[2] / max(adj_phase_launch, 1)
-    per_launch_pts = w.padded_points * B
+    per_launch_pts = w.padded_points * plan["samples_per_chunk"] * nsg  # wavefields of one launch
+    # the adjoint phase also holds the recompute (forward) launches: split it by
+    # charging them the forward kernel's average launch time
+    rec_launches = adj_phase_launch - w.nt * nchunks * n
+    adj_only_ms = phase_ms[2] - max(rec_launches, 0) * fwd_launch_ms
+    adj_launch_ms = adj_only_ms / max(adj_phase_launch - max(rec_launches, 0), 1)
+    kd = "3d" if w.ndim == 3 else "2d"
     kern = {
-        "step2d_kernel<ADJ>": {"ms": adj_launch_ms, "bytes": bpu["adjoint"] * per_launch_pts,
-                               "share": phase_ms[2] / max(phase_ms.sum(), 1e-9)},
-        "step2d_kernel<FWD>": {"ms": fwd_launch_ms, "bytes": bpu["forward"] * per_launch_pts,
-                               "share": phase_ms[0] / max(phase_ms.sum(), 1e-9)},
+        "step%s_kernel<ADJ>" % kd: {"ms": adj_launch_ms, "bytes": bpu["adjoint"] * per_launch_pts,
+                                    "share": adj_only_ms / max(phase_ms.sum(), 1e-9)},
+        "step%s_kernel<FWD>" % kd: {"ms": fwd_launch_ms, "bytes": bpu["forward"] * per_launch_pts,
+                                    "share": (phase_ms[0] + phase_ms[2] - adj_only_ms) / max(phase_ms.sum(), 1e-9)},
     }
     dom = max(kern, key=lambda k: kern[k]["share"])
     peaks = _peaks()
@@ -314,7 +324,7 @@ def native_arm(args):
                                        "tuner_ms_adjoint": variants["adjoint_ms"]}},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": ms_e2e},
-           "gpu_launches": int(phase_launch.sum() + n * 3),
+           "gpu_launches": int(phase_launch.sum() + n * 2),
            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",

@@ -217,9 +217,16 @@ const char* fwi_last_cuda_error(void);
 int fwi_last_device_status(fwi_ctx* ctx, void* stream);
 
 /* Checkpoint plan of the last fwi_gradient call: snapshot segment length,
- * number of segments, forward steps recomputed, wavefield slots used. */
+ * number of segments, forward steps recomputed, wavefield slots used (all
+ * per chunk of samples, see fwi_chunking). */
 int fwi_plan_info(fwi_ctx* ctx, int* segment_len, int* nsegments, int64_t* recomputed_steps,
                   int* slots_used, int* slots_available);
+
+/* Samples per chunk of the last fwi_gradient call.  When the checkpoint plan
+ * of all nsamp*nsg wavefields does not fit the workspace (large 3D batches),
+ * fwi_gradient processes the samples in chunks, choosing the chunk size that
+ * minimises (chunks) x (2 nt + recomputed steps) x (time of one step launch). */
+int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
 
 /* Step-kernel variants (tile rows per thread, TMA ring depth).  By default the
  * first fwi_forward / fwi_gradient call for a given nsamp*nsg times every

@@ -126,8 +126,10 @@ class FWI:
         rec = ctypes.c_int64()
         check(lib().fwi_plan_info(self._h, ctypes.byref(K), ctypes.byref(S), ctypes.byref(rec), ctypes.byref(used),
                                   ctypes.byref(avail)), "fwi_plan_info")
+        ch = ctypes.c_int()
+        check(lib().fwi_chunking(self._h, ctypes.byref(ch)), "fwi_chunking")
         return {"segment_len": K.value, "segments": S.value, "recomputed_steps": rec.value,
-                "slots_used": used.value, "slots_available": avail.value}
+                "slots_used": used.value, "slots_available": avail.value, "samples_per_chunk": ch.value}
 
     def set_variants(self, fwd=-1, adj=-1):
         """Force step-kernel variants (-1: autotune on the next call)."""

@@ -15,7 +15,7 @@ FWI_STATUS = {0: "FWI_OK", -1: "FWI_ERR_ARG", -2: "FWI_ERR_CFL", -3: "FWI_ERR_OO
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradient", "langevin_step", "renoise",
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
            "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error",
-           "fwi_set_kernel_variants", "fwi_kernel_variants"]
+           "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -58,6 +58,7 @@ _SIGS = {
     "fwi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fwi_last_cuda_error": (ctypes.c_char_p, []),
     "fwi_set_kernel_variants": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "fwi_chunking": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "fwi_kernel_variants": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_char_p),
                                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),

@@ -154,6 +154,9 @@ struct fwi_ctx {
   long long launches[4] = {0, 0, 0, 0};
   Plan plan;
   long long slots_avail = 0;
+  int chunk_samples = 0;
+  bool last_was_gradient = false;
+  float prof_ms[4] = {0.f, 0.f, 0.f, 0.f};
   // step-kernel variants: chosen per call shape by timing (autotune), or forced
   int var[2] = {-1, -1};
   int forced[2] = {-1, -1};
@@ -785,6 +788,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
   for (int i = 0; i < 4; i++) C->launches[i] = 0;
+  C->last_was_gradient = false;
   prof_mark(C, 0, st);
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, nullptr, d_pred, st)) != FWI_OK) return rc;
@@ -795,36 +799,31 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   return FWI_OK;
 }
 
-int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
-                 int nsg, const float* d_obs, double sigma_y, double scale, float* grad, double* misfit,
-                 void* stream) {
-  int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
-  if (rc != FWI_OK) return rc;
-  if (!d_obs || !grad || !misfit || !(sigma_y > 0)) return FWI_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+// One chunk of samples through forward, residual/misfit, reverse sweep and
+// fold.  The pool is partitioned for Bpart >= nsamp*nsg wavefields, so every
+// chunk of a call (the last one may be smaller) shares one slot layout.
+static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w,
+                          const int32_t* sg, int nsg, const float* d_obs, double sigma_y, double scale, float* grad,
+                          double* misfit, cudaStream_t st, int Bpart) {
+  int rc;
   const int B = nsamp * nsg;
   const int nt = C->g.nt, nr = C->nr;
-  if (!(scale > 0)) {
-    long long tot = 0;
-    for (int j = 0; j < nsg; j++) tot += sg[j];
-    scale = (double)C->ns / (double)tot;
-  }
   long long nslots;
-  if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
+  if ((rc = partition_pool(C, Bpart, st, &nslots)) != FWI_OK) return rc;
   Plan plan;
   if (!make_plan(nt, nslots, &plan)) return FWI_ERR_OOM;
   C->plan = plan;
   C->slots_avail = nslots;
   CUtensorMap th, tp, tc;
-  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
-  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, st)) != FWI_OK) return rc;
+  if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
+  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
-  for (int i = 0; i < 4; i++) C->launches[i] = 0;
 
   prof_mark(C, 0, st);
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
+  C->launches[0] += 1;
   const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
   CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, &plan, C->dpred, st)) != FWI_OK) return rc;
@@ -836,7 +835,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
                      reinterpret_cast<const int*>(C->dlist + cl.shot_id),
                      reinterpret_cast<const float*>(C->dlist + cl.shot_w), inv_s2, C->dpred, C->part, C->nblk, st));
   CK(launch_misfit(nsamp, nsg, C->part, C->nblk, scale * 0.5 * inv_s2, misfit, C->status, st));
-  C->launches[1] = 2;
+  C->launches[1] += 2;
   prof_mark(C, 2, st);
 
   // reverse sweep: recompute each earlier segment, then the adjoint steps
@@ -885,7 +884,7 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
       adj_launch++;
     }
   }
-  C->launches[2] = adj_launch;
+  C->launches[2] += adj_launch;
   prof_mark(C, 3, st);
   CK(launch_source_imaging(B, nsg, nt, C->Emax, C->qsrc, C->wav,
                            reinterpret_cast<const int*>(C->dlist + cl.src_cnt),
@@ -893,8 +892,64 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
                            reinterpret_cast<const float*>(C->dlist + cl.src_amp), C->stmp, C->G, C->L.field,
                            g_per_wf, st));
   CK(launch_finalize(C->L, vel, C->G, nsamp, g_per_wf ? nsg : 1, scale, grad, st));
-  C->launches[3] = 3;
+  C->launches[3] += 3;
   prof_mark(C, 4, st);
+  if (C->prof) {  // accumulate this chunk's phase times
+    CK(cudaEventSynchronize(C->ev[4]));
+    for (int i = 0; i < 4; i++) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, C->ev[i], C->ev[i + 1]));
+      C->prof_ms[i] += ms;
+    }
+  }
+  return FWI_OK;
+}
+
+int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                 int nsg, const float* d_obs, double sigma_y, double scale, float* grad, double* misfit,
+                 void* stream) {
+  int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
+  if (rc != FWI_OK) return rc;
+  if (!d_obs || !grad || !misfit || !(sigma_y > 0)) return FWI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nt = C->g.nt;
+  if (!(scale > 0)) {
+    long long tot = 0;
+    for (int j = 0; j < nsg; j++) tot += sg[j];
+    scale = (double)C->ns / (double)tot;
+  }
+  // Samples per chunk: the whole batch when its checkpoint plan fits the pool,
+  // otherwise the chunk size that minimises (chunks) x (2 nt + recomputed
+  // steps) x (time of one step launch), a launch costing at least ~8 us.
+  const double pts = (double)C->L.nzp * C->L.nyp * C->L.nxp;
+  int best_c = -1;
+  double best_cost = 0.0;
+  for (int c = nsamp; c >= 1; c--) {
+    const size_t slot_bytes = (size_t)C->L.field * c * nsg * 4;
+    Plan p;
+    if (!make_plan(nt, (long long)(C->pool_bytes / slot_bytes), &p)) continue;
+    const int nchunks = (nsamp + c - 1) / c;
+    const double t_launch = std::max(8e-6, c * nsg * pts * 16.0 / 6e12);
+    const double cost = nchunks * (2.0 * nt + (double)p.recompute) * t_launch;
+    if (best_c < 0 || cost < best_cost * 0.999) {
+      best_c = c;
+      best_cost = cost;
+    }
+  }
+  if (best_c < 0) return FWI_ERR_OOM;
+  for (int i = 0; i < 4; i++) {
+    C->launches[i] = 0;
+    C->prof_ms[i] = 0.f;
+  }
+  C->chunk_samples = best_c;
+  C->last_was_gradient = true;
+  const long long phys = C->L.phys;
+  for (int s0 = 0; s0 < nsamp; s0 += best_c) {
+    const int n = std::min(best_c, nsamp - s0);
+    rc = gradient_chunk(C, vel + (size_t)s0 * phys, n, perm + (size_t)s0 * C->ns, w + (size_t)s0 * C->ns, sg, nsg,
+                        d_obs, sigma_y, scale, grad + (size_t)s0 * phys, misfit + s0, st, best_c * nsg);
+    if (rc != FWI_OK) return rc;
+  }
   return FWI_OK;
 }
 
@@ -973,6 +1028,12 @@ int fwi_kernel_variants(fwi_ctx* C, int* fwd, int* adj, const char** fwd_name, c
   return FWI_OK;
 }
 
+int fwi_chunking(fwi_ctx* C, int* samples_per_chunk) {
+  if (!C || !samples_per_chunk) return FWI_ERR_ARG;
+  *samples_per_chunk = C->chunk_samples;
+  return FWI_OK;
+}
+
 int fwi_set_profiling(fwi_ctx* C, int on) {
   if (!C) return FWI_ERR_ARG;
   C->prof = on != 0;
@@ -983,7 +1044,13 @@ int fwi_phase_times(fwi_ctx* C, float* ms, int64_t* launches) {
   if (!C || !C->prof) return FWI_ERR_ARG;
   CK(cudaEventSynchronize(C->ev[4]));
   for (int i = 0; i < 4; i++) {
-    if (ms) CK(cudaEventElapsedTime(&ms[i], C->ev[i], C->ev[i + 1]));
+    if (ms) {
+      if (C->last_was_gradient) {
+        ms[i] = C->prof_ms[i];
+      } else {
+        CK(cudaEventElapsedTime(&ms[i], C->ev[i], C->ev[i + 1]));
+      }
+    }
     if (launches) launches[i] = C->launches[i];
   }
   return FWI_OK;

@@ -232,3 +232,24 @@ def test_all_step_kernel_variants_bit_identical(P, torch):
     info = ctx.variants()
     assert min(x for x in info["forward_ms"] if x > 0) > 0
     assert torch.equal(g, ref[1])
+
+
+def test_chunked_gradient_bit_identical(P, torch):
+    # a workspace too small for all samples at once makes fwi_gradient process
+    # them in chunks; every sample's arithmetic is unchanged
+    w = synth.tiny2d(nz=40, nx=70, nt=150, ns=4, nr=12, nb=6)
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 50 + s, 1500, 2500)
+                               for s in range(3)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 6)).cuda()
+    encs = [P.encode(4, s, w.ns) for s in range(3)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    big = make_ctx(P, w, 6, budget=1 << 30)
+    m1, g1 = big.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    assert big.plan_info()["samples_per_chunk"] == 3
+    field = (w.nz + 2 * w.nb + 8) * (((w.nx + 2 * w.nb + 8) + 31) // 32 * 32) * 4
+    small = make_ctx(P, w, 6, budget=60 * 2 * field)
+    m2, g2 = small.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    torch.cuda.synchronize()
+    assert small.plan_info()["samples_per_chunk"] == 1
+    assert torch.equal(g1, g2) and torch.equal(m1, m2)
