@@ -252,7 +252,8 @@ void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, i
   }
 }
 
-int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain, CUtensorMap* ctile) {
+int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain, CUtensorMap* ctile,
+               CUtensorMap* gtile) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return FWI_ERR_CUDA;
   const Layout& L = C->L;
@@ -276,6 +277,7 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return FWI_ERR_CUDA;
+    *gtile = *ctile;  // unused by the 2D kernels
     return FWI_OK;
   }
   const cuuint64_t dims[5] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)B,
@@ -291,7 +293,18 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return FWI_ERR_CUDA;
-  *ctile = *plain;  // unused by the 3D kernels
+  // cc per sample and the imaging accumulator per wavefield, plain planes
+  const cuuint64_t d4[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
+  const cuuint64_t s4[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4};
+  const cuuint32_t b4[4] = {TX, TY3, 1, 1};
+  if (enc(ctile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->c, d4, s4, b4, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return FWI_ERR_CUDA;
+  if (enc(gtile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->G, d4, s4, b4, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return FWI_ERR_CUDA;
   return FWI_OK;
 }
 
@@ -448,8 +461,8 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
 }
 
 cudaError_t launch_step(fwi_ctx* C, bool adj, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
-                        const StepParams& P, int nsamp, int B, cudaStream_t st) {
-  if (C->L.ndim == 3) return launch_step3d(adj, th, tp, C->L, C->K, P, B, st);
+                        const CUtensorMap& tg, const StepParams& P, int nsamp, int B, cudaStream_t st) {
+  if (C->L.ndim == 3) return launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st);
   return launch_step2d(adj, C->var[adj ? 1 : 0], th, tp, tc, C->L, C->K, P, nsamp, st);
 }
 
@@ -735,8 +748,8 @@ void fwi_destroy(fwi_ctx* C) {
 }
 
 static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const CUtensorMap& th,
-                            const CUtensorMap& tp, const CUtensorMap& tc, const Plan* plan, float* dout,
-                            cudaStream_t st) {
+                            const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, const Plan* plan,
+                            float* dout, cudaStream_t st) {
   const int B = nsamp * nsg;
   StepParams P = base_params(C, B, nsg);
   P.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
@@ -765,7 +778,7 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
       P.s_out = 1 + (n + 1) % 3;
     }
     P.t = n;
-    CK(launch_step(C, false, th, tp, tc, P, nsamp, B, st));
+    CK(launch_step(C, false, th, tp, tc, tg, P, nsamp, B, st));
   }
   C->launches[0] += C->g.nt;
   return FWI_OK;
@@ -781,8 +794,8 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   long long nslots;
   if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
   if (nslots < 4) return FWI_ERR_OOM;
-  CUtensorMap th, tp, tc;
-  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
+  CUtensorMap th, tp, tc, tg;
+  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
   if ((rc = autotune(C, nsamp, nsg, th, tp, tc, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
@@ -791,7 +804,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   C->last_was_gradient = false;
   prof_mark(C, 0, st);
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, nullptr, d_pred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, nullptr, d_pred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
   prof_mark(C, 2, st);
   prof_mark(C, 3, st);
@@ -814,8 +827,8 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if (!make_plan(nt, nslots, &plan)) return FWI_ERR_OOM;
   C->plan = plan;
   C->slots_avail = nslots;
-  CUtensorMap th, tp, tc;
-  if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc)) != FWI_OK) return rc;
+  CUtensorMap th, tp, tc, tg;
+  if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
   if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
@@ -826,7 +839,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   C->launches[0] += 1;
   const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
   CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, &plan, C->dpred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, &plan, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
   // residual (rhat overwrites dpred) and misfit
@@ -870,7 +883,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
         F.s_prev = plan.rslot(j, n - 1);
         F.s_out = plan.rslot(j, n + 1);
         F.t = n;
-        CK(launch_step(C, false, th, tp, tc, F, nsamp, B, st));
+        CK(launch_step(C, false, th, tp, tc, tg, F, nsamp, B, st));
         adj_launch++;
       }
     }
@@ -880,7 +893,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
       A.s_out = plan.qslot(k);
       A.s_snap = plan.snap(j, k - 1);
       A.t = k - 1;
-      CK(launch_step(C, true, th, tp, tc, A, nsamp, B, st));
+      CK(launch_step(C, true, th, tp, tc, tg, A, nsamp, B, st));
       adj_launch++;
     }
   }

@@ -74,7 +74,8 @@ cudaError_t launch_step2d(bool adj, int variant, const CUtensorMap& tm_halo, con
 int num_variants2d(bool adj);
 const char* variant2d_name(bool adj, int v);
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
-                          const Layout& L, const Coef& K, const StepParams& P, int B, cudaStream_t st);
+                          const CUtensorMap& tm_cc, const CUtensorMap& tm_g, const Layout& L, const Coef& K,
+                          const StepParams& P, int B, cudaStream_t st);
 
 // Auxiliary kernels (aux.cu)
 cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, const float* gtab, float* c,

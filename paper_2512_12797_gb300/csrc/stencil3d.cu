@@ -1,35 +1,41 @@
 // stencil3d.cu -- 3D time-step kernels (forward recursion; adjoint recursion
 // with the imaging condition), same algebra as the 2D kernels in stencil.cu:
 //     p^{n+1} = p^n + b (p^n - p^{n-1}) + cc (L p^n + s^n),  L = sum_a sum_k a_k/h_a^2 [(p_{+k} + p_{-k}) - 2p]
-// (cc = v^2 dt^2/(1 + gamma dt) is read from the expanded array; b = (1 - gamma dt)/(1 + gamma dt)
-// from the per-axis gamma*dt table)
-//     q^k     = q^{k+1} + b (q^{k+1} - q^{k+2}) + cc (L q^{k+1} + R^T rhat^{k-1}),  G += q^k L p^{k-1}.
+//     q^k     = q^{k+1} + b (q^{k+1} - q^{k+2}) + cc (L q^{k+1} + R^T rhat^{k-1}),  G += q^k L p^{k-1}
+// (cc = v^2 dt^2/(1 + gamma dt) comes from the expanded array, b = (1 - gamma dt)/(1 + gamma dt)
+// from the per-axis gamma*dt table).
 //
 // 2.5D blocking: a CTA owns a 128 (x) x 8 (y) column of one wavefield and
-// marches through z.  Each thread owns 4 consecutive x points of one y row and
-// keeps the 9 z-levels its z-derivative needs in a register queue.  x-y halo
-// planes (136 x 16) of the field being stepped, and plain planes (128 x 8) of
-// the older level, stream through an 8-slot shared-memory ring by TMA, three
-// planes ahead of the compute; in the adjoint the snapshot p^{k-1} has its own
-// halo-plane ring and register queue for L p^{k-1}.  Sequence number q of the
-// ring carries the halo plane z = q - 4 and the plain plane z = q - 8; level
-// z = q - 8 is computed once sequence q has landed.
+// marches through z; each thread owns 4 consecutive x points of one y row and
+// keeps the 9 z-levels its z-derivative needs in a circular register queue
+// (the level loop is unrolled by 9 so the queue never moves).  Ring
+// sequence q carries the x-y halo plane (136 x 16) of level q-4 -- whose
+// centre enters the queue at q and whose x-y neighbours serve level q-4 at
+// q+4 -- and the plain planes (128 x 8) of level q-8: p^{n-1}, cc and, in the
+// adjoint, the imaging accumulator; the adjoint also streams halo planes of
+// the snapshot p^{k-1} with its own register queue for L p^{k-1}.  Level
+// z = q - 8 is computed once sequence q has landed.  Every warp releases the
+// slot of sequence q-4 after computing level q-8 (per-warp "empty" mbarrier
+// arrivals); lane 0 of the last warp refills slots as they free up, blocking
+// only for the sequence its own warp needs next.
 #include "fwi_internal.cuh"
 
 namespace fwi {
 
 constexpr int HY3 = TY3 + 2 * HALO;  // 16
-constexpr int PLANE = HY3 * HX;     // floats in a halo plane
-constexpr int PPLANE = TY3 * TX;    // floats in a plain plane
-constexpr int NST = 8;              // ring slots
+constexpr int PLANE = HY3 * HX;      // floats in a halo plane
+constexpr int PPLANE = TY3 * TX;     // floats in a plain plane
 
 template <bool ADJ>
 struct Smem3D {
-  static constexpr int off_prev = NST * PLANE;
-  static constexpr int off_snap = off_prev + NST * PPLANE;
-  static constexpr int off_stage = off_snap + (ADJ ? NST * PLANE : 0);
-  static constexpr int nfloat = off_stage + PPLANE;
-  static constexpr int bytes = nfloat * 4 + NST * 8;
+  static constexpr int NST = ADJ ? 7 : 10;  // ring slots
+  static constexpr int OFF_SNAP = PLANE;
+  static constexpr int OFF_PREV = PLANE * (ADJ ? 2 : 1);
+  static constexpr int OFF_CC = OFF_PREV + PPLANE;
+  static constexpr int OFF_G = OFF_CC + PPLANE;
+  static constexpr int STAGE = OFF_G + (ADJ ? PPLANE : 0);
+  static constexpr int OFF_GZ = NST * STAGE;  // gamma*dt of every z level
+  static size_t bytes(int nzp) { return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + 2 * NST * 8; }
 };
 
 __device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -39,13 +45,14 @@ __device__ __forceinline__ float comp(const float4& v, int j) {
 }
 
 // Laplacian of the thread's 4 points: x and y neighbours from the halo plane H
-// (row ly+4, columns lx..lx+11), z neighbours from the register queue Q[0..8]
-// (Q[4] is the centre level).
+// (row ly+4, columns lx..lx+11), z neighbours from the circular register queue
+// Q (Q[(C+k) % 9] holds level z+k, k = -4..4, C the index of the centre).
+template <int C>
 __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[9], int ly, int lx,
                                      const Coef& K, float (&lap)[4]) {
   const float* row = H + (ly + HALO) * HX;
   const float4 xl = ld4s(row + lx), xr = ld4s(row + lx + 8);
-  const float4 ce = Q[4];
+  const float4 ce = Q[C % 9];
   const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
   float4 yn[8];
 #pragma unroll
@@ -64,158 +71,145 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
     a = fmaf(K.cy[3], (comp(yn[6], j) + comp(yn[2], j)) - p2, a);
     a = fmaf(K.cy[2], (comp(yn[5], j) + comp(yn[1], j)) - p2, a);
     a = fmaf(K.cy[1], (comp(yn[4], j) + comp(yn[0], j)) - p2, a);
-    a = fmaf(K.cz[4], (comp(Q[8], j) + comp(Q[0], j)) - p2, a);
-    a = fmaf(K.cz[3], (comp(Q[7], j) + comp(Q[1], j)) - p2, a);
-    a = fmaf(K.cz[2], (comp(Q[6], j) + comp(Q[2], j)) - p2, a);
-    a = fmaf(K.cz[1], (comp(Q[5], j) + comp(Q[3], j)) - p2, a);
+    a = fmaf(K.cz[4], (comp(Q[(C + 4) % 9], j) + comp(Q[(C + 5) % 9], j)) - p2, a);
+    a = fmaf(K.cz[3], (comp(Q[(C + 3) % 9], j) + comp(Q[(C + 6) % 9], j)) - p2, a);
+    a = fmaf(K.cz[2], (comp(Q[(C + 2) % 9], j) + comp(Q[(C + 7) % 9], j)) - p2, a);
+    a = fmaf(K.cz[1], (comp(Q[(C + 1) % 9], j) + comp(Q[(C + 8) % 9], j)) - p2, a);
     lap[j] = a;
   }
 }
 
 template <bool ADJ>
-__global__ void __launch_bounds__(NTHREADS, 1)
-step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
-              const Layout L, const Coef K, const StepParams P) {
+struct March3D {
   using S = Smem3D<ADJ>;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float* s_cur = reinterpret_cast<float*>(smem_raw);
-  float* s_prev = s_cur + S::off_prev;
-  float* s_snap = s_cur + S::off_snap;
-  float* s_stage = s_cur + S::off_stage;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + S::nfloat * 4);
-
-  const int tid = threadIdx.x, lane = tid & 31, ly = tid >> 5;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY3, b = blockIdx.z;
-  const int s = b / P.nsg;
-  const int tile = blockIdx.y * P.ntx + blockIdx.x;
-  const int lx = 4 * lane;
-  const int gx = x0 + lx, gy = y0 + ly;
-  const bool colv = gx < L.nxp && gy < L.nyp;
-
-  if (tid == 0) {
-    tma_prefetch_desc(&tm_halo);
-    tma_prefetch_desc(&tm_plain);
-    for (int i = 0; i < NST; i++) mbar_init(&bar[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  const int last_q = L.nzp + 7;
-  auto issue = [&](int q) {
-    const int slot = q % NST;
-    const int zh = q - HALO;       // halo plane level
-    const int zp = q - 2 * HALO;   // plain plane level
-    const bool with_prev = zp >= 0 && zp < L.nzp;
-    uint32_t bytes = PLANE * 4 * (ADJ ? 2 : 1) + (with_prev ? PPLANE * 4 : 0);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bar[slot], bytes);
-    tma_load_5d(s_cur + slot * PLANE, &tm_halo, x0, y0, zh + HALO, b, P.s_cur, &bar[slot]);
-    if (ADJ) tma_load_5d(s_snap + slot * PLANE, &tm_halo, x0, y0, zh + HALO, b, P.s_snap, &bar[slot]);
-    if (with_prev)
-      tma_load_5d(s_prev + slot * PPLANE, &tm_plain, x0 + HALO, y0 + HALO, zp + HALO, b, P.s_prev, &bar[slot]);
-  };
-  if (tid == 0)
-    for (int q = 0; q < NST && q <= last_q; q++) issue(q);
-
-  // per-call point lists of this tile (entries sorted by z)
-  const int ib = P.inj_off[b * P.inj_bstride + tile], ie = P.inj_off[b * P.inj_bstride + tile + 1];
-  int sb = 0, se = 0;
-  if (P.smp4) {
-    sb = P.smp_off[b * P.smp_bstride + tile];
-    se = P.smp_off[b * P.smp_bstride + tile + 1];
-  }
-  const float* cs = P.c + (long long)s * L.field;
-  float* outp = P.pool + (long long)P.s_out * P.slot_elems + (long long)b * L.field;
-  float* gb = ADJ ? P.grad + (long long)b * L.field : nullptr;
-
-  // sponge table entries of this thread's y row and x columns
-  const float gyv = gy < L.nyp ? __ldg(P.gtab + L.nzp + gy) : 0.f;
-  float gxv[4];
-#pragma unroll
-  for (int j = 0; j < 4; j++) gxv[j] = gx + j < L.nxp ? __ldg(P.gtab + L.nzp + L.nyp + gx + j) : 0.f;
-
+  static constexpr int NST = S::NST;
+  const Layout& L;
+  const Coef& K;
+  const StepParams& P;
+  const CUtensorMap* th;
+  const CUtensorMap* tp;
+  const CUtensorMap* tcc;
+  const CUtensorMap* tg;
+  float* sm;
+  uint64_t* full;
+  uint64_t* empty;
+  int lane, ly, lx, x0, y0, gx, gy, b, s, tile, last_q;
+  bool colv, producer;
+  float gyv, gxv[4];
+  const float* gz;       // shared gamma*dt per z level
+  int pq, pst;           // producer: next sequence, its slot
+  uint32_t pround;
+  int ie_cur, ie_end, se_cur, se_end;  // point-list cursors (entries sorted by z)
+  int inj_z, smp_z;                    // z of the entries under the cursors (INT_MAX: none left)
   float4 Q[9], QS[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    QS[i] = Q[i];
+
+  __device__ __forceinline__ void issue() {
+    const int zh = pq - HALO, zp = pq - 2 * HALO;
+    const bool plain = zp >= 0 && zp < L.nzp;
+    float* base = sm + pst * S::STAGE;
+    uint32_t bytes = PLANE * 4 * (ADJ ? 2 : 1) + (plain ? PPLANE * 4 * (ADJ ? 3 : 2) : 0);
+    mbar_arrive_expect_tx(&full[pst], bytes);
+    tma_load_5d(base, th, x0, y0, zh + HALO, b, P.s_cur, &full[pst]);
+    if (ADJ) tma_load_5d(base + S::OFF_SNAP, th, x0, y0, zh + HALO, b, P.s_snap, &full[pst]);
+    if (plain) {
+      tma_load_5d(base + S::OFF_PREV, tp, x0 + HALO, y0 + HALO, zp + HALO, b, P.s_prev, &full[pst]);
+      tma_load_4d(base + S::OFF_CC, tcc, x0 + HALO, y0 + HALO, zp + HALO, s, &full[pst]);
+      if (ADJ) tma_load_4d(base + S::OFF_G, tg, x0 + HALO, y0 + HALO, zp + HALO, b, &full[pst]);
+    }
+    pq++;
+    if (++pst == NST) { pst = 0; pround ^= 1; }
   }
 
-  for (int q = 0; q <= last_q; q++) {
-    const int slot = q % NST;
-    const bool ok = mbar_wait_bounded(&bar[slot], (q / NST) & 1, P.status);
-    if (__syncthreads_or(!ok)) return;
-    // shift the queues and append the centre of halo plane q-4 (level q-4)
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      Q[i] = Q[i + 1];
-      if (ADJ) QS[i] = QS[i + 1];
+  // Issue every sequence whose slot all warps have released; block only for `need`.
+  __device__ __forceinline__ bool refill(int need) {
+    while (pq <= last_q && pq <= need + NST - 5) {
+      if (pq >= NST) {
+        if (pq <= need) {
+          if (!mbar_wait_bounded(&empty[pst], pround ^ 1, P.status)) return false;
+        } else if (!mbar_try_wait(&empty[pst], pround ^ 1)) {
+          break;
+        }
+      }
+      issue();
     }
-    Q[8] = ld4s(s_cur + slot * PLANE + (ly + HALO) * HX + lx + HALO);
-    if (ADJ) QS[8] = ld4s(s_snap + slot * PLANE + (ly + HALO) * HX + lx + HALO);
+    return true;
+  }
 
-    const int z = q - 2 * HALO;  // level computed at this sequence
+  // Sequence q with the queue centre at compile-time index C = (q - 4) % 9.
+  template <int C>
+  __device__ __forceinline__ bool step(int q) {
+    const int slot = q % NST;
+    if (producer && !refill(q)) return false;
+    if (!mbar_wait_bounded(&full[slot], (uint32_t)((q / NST) & 1), P.status)) return false;
+    float* stage = sm + slot * S::STAGE;
+    // the centre of halo plane q-4 enters the queue at index (C + 4) % 9
+    Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX + lx + HALO);
+    if (ADJ) QS[(C + 4) % 9] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX + lx + HALO);
+    const int z = q - 2 * HALO;
     if (z >= 0) {
-      const int hslot = (q - HALO) % NST;  // halo plane of level z
+      const float* hpl = sm + ((q - HALO) % NST) * S::STAGE;  // halo plane of level z
       float lap[4];
-      lap3(s_cur + hslot * PLANE, Q, ly, lx, K, lap);
-      const float4 pm = ld4s(s_prev + slot * PPLANE + ly * TX + lx);
-      float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (colv) cv = __ldg(reinterpret_cast<const float4*>(cs + L.off(z, gy, gx)));
-      const float gzy = __ldg(P.gtab + z) + gyv;
+      lap3<C>(hpl, Q, ly, lx, K, lap);
+      const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX + lx);
+      const float4 cv = ld4s(stage + S::OFF_CC + ly * TX + lx);
+      const float gzy = gz[z] + gyv;
       float nv[4];
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         const float bb = sponge_b(gzy + gxv[j]);
-        const float p = comp(Q[4], j);
+        const float p = comp(Q[C % 9], j);
         nv[j] = fmaf(comp(cv, j), lap[j], fmaf(bb, p - comp(pm, j), p));
       }
-      // injection / sampling at this level (only tiles with points at level z)
-      bool mine = false;
-      for (int e = ib + tid; e < ie; e += NTHREADS) mine |= P.inj[e].w == z;
-      for (int e = sb + tid; e < se; e += NTHREADS) mine |= P.smp4[e].z == z;
-      if (__syncthreads_or(mine)) {
-        *reinterpret_cast<float4*>(s_stage + ly * TX + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
-        __syncthreads();
-        for (int e = ib + tid; e < ie; e += NTHREADS) {
+      // injection / sampling at this level: staged in this warp's row of the
+      // p^{n-1} plane (already consumed)
+      if (inj_z == z || smp_z == z) {
+        float* row = stage + S::OFF_PREV + ly * TX;
+        __syncwarp();
+        *reinterpret_cast<float4*>(row + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        __syncwarp();
+        int e_end = ie_cur;
+        while (e_end < ie_end && P.inj[e_end].w == z) e_end++;
+        for (int e = ie_cur + lane; e < e_end; e += 32) {
           const int4 en = P.inj[e];
-          if (en.w != z) continue;
-          const int yy = y0 + en.x / TX, xx = x0 + en.x % TX;
-          const float ccp = __ldg(cs + L.off(z, yy, xx));
-          s_stage[en.x] += ccp * (__int_as_float(en.z) *
-                                  P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
+          if (en.x / TX != ly) continue;
+          const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + ly, x0 + en.x % TX));
+          row[en.x % TX] += ccp * (__int_as_float(en.z) *
+                                   P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
         }
-        __syncthreads();
-        const float4 v = ld4s(s_stage + ly * TX + lx);
+        ie_cur = e_end;
+        inj_z = ie_cur < ie_end ? P.inj[ie_cur].w : 0x7fffffff;
+        __syncwarp();
+        const float4 v = ld4s(row + lx);
         nv[0] = v.x; nv[1] = v.y; nv[2] = v.z; nv[3] = v.w;
-        for (int e = sb + tid; e < se; e += NTHREADS) {
+        int s_end = se_cur;
+        while (s_end < se_end && P.smp4[s_end].z == z) s_end++;
+        for (int e = se_cur + lane; e < s_end; e += 32) {
           const int4 en = P.smp4[e];
-          if (en.z != z) continue;
-          P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = s_stage[en.x];
+          if (en.x / TX != ly) continue;
+          P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = row[en.x % TX];
         }
+        se_cur = s_end;
+        smp_z = se_cur < se_end ? P.smp4[se_cur].z : 0x7fffffff;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       if (ADJ) {
         float lps[4];
-        lap3(s_snap + hslot * PLANE, QS, ly, lx, K, lps);
+        lap3<C>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
+        const float4 g = ld4s(stage + S::OFF_G + ly * TX + lx);
         if (colv) {
-          float4* gp = reinterpret_cast<float4*>(gb + L.off(z, gy, gx));
-          float4 g = *gp;
-          g.x = fmaf(nv[0], lps[0], g.x);
-          g.y = fmaf(nv[1], lps[1], g.y);
-          g.z = fmaf(nv[2], lps[2], g.z);
-          g.w = fmaf(nv[3], lps[3], g.w);
+          float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
+          const float gv[4] = {fmaf(nv[0], lps[0], g.x), fmaf(nv[1], lps[1], g.y), fmaf(nv[2], lps[2], g.z),
+                               fmaf(nv[3], lps[3], g.w)};
           if (gx + 3 < L.nxp) {
-            *gp = g;
+            *reinterpret_cast<float4*>(gp) = make_float4(gv[0], gv[1], gv[2], gv[3]);
           } else {
-            float* gs = reinterpret_cast<float*>(gp);
-            const float gv[4] = {g.x, g.y, g.z, g.w};
             for (int j = 0; j < 4; j++)
-              if (gx + j < L.nxp) gs[j] = gv[j];
+              if (gx + j < L.nxp) gp[j] = gv[j];
           }
         }
       }
       if (colv) {
-        float* o = outp + L.off(z, gy, gx);
+        float* o = P.pool + (long long)P.s_out * P.slot_elems + (long long)b * L.field + L.off(z, gy, gx);
         if (gx + 3 < L.nxp) {
           *reinterpret_cast<float4*>(o) = make_float4(nv[0], nv[1], nv[2], nv[3]);
         } else {
@@ -224,28 +218,117 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
         }
       }
     }
-    __syncthreads();  // slot of sequence q-4 (halo of level z) is free
-    if (tid == 0 && q >= HALO && q + HALO <= last_q) issue(q + HALO);
+    // release the slot of sequence q-4: its halo plane served level q-8 above
+    if (q >= HALO) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[(q - HALO) % NST]);
+    }
+    return true;
   }
+};
+
+template <bool ADJ>
+__global__ void __launch_bounds__(NTHREADS, 1)
+step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
+              const __grid_constant__ CUtensorMap tm_cc, const __grid_constant__ CUtensorMap tm_g, const Layout L,
+              const Coef K, const StepParams P) {
+  using S = Smem3D<ADJ>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  float* gz = sm + S::OFF_GZ;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)S::OFF_GZ + ((L.nzp + 31) / 32) * 32) * 4));
+  uint64_t* empty = full + S::NST;
+
+  const int tid = threadIdx.x;
+  March3D<ADJ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty};
+  M.lane = tid & 31;
+  M.ly = tid >> 5;
+  M.x0 = blockIdx.x * TX;
+  M.y0 = blockIdx.y * TY3;
+  M.b = blockIdx.z;
+  M.s = M.b / P.nsg;
+  M.tile = blockIdx.y * P.ntx + blockIdx.x;
+  M.lx = 4 * M.lane;
+  M.gx = M.x0 + M.lx;
+  M.gy = M.y0 + M.ly;
+  M.colv = M.gx < L.nxp && M.gy < L.nyp;
+  M.last_q = L.nzp + 7;
+  M.producer = tid == NTHREADS - 32;
+  M.gz = gz;
+  M.pq = 0;
+  M.pst = 0;
+  M.pround = 0;
+
+  if (tid == 0) {
+    tma_prefetch_desc(&tm_halo);
+    tma_prefetch_desc(&tm_plain);
+    tma_prefetch_desc(&tm_cc);
+    if (ADJ) tma_prefetch_desc(&tm_g);
+    for (int i = 0; i < S::NST; i++) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NTHREADS / 32);
+    }
+    fence_mbar_init();
+  }
+  for (int i = tid; i < L.nzp; i += NTHREADS) gz[i] = P.gtab[i];
+  __syncthreads();
+
+  M.gyv = M.gy < L.nyp ? __ldg(P.gtab + L.nzp + M.gy) : 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; j++) M.gxv[j] = M.gx + j < L.nxp ? __ldg(P.gtab + L.nzp + L.nyp + M.gx + j) : 0.f;
+  M.ie_cur = P.inj_off[M.b * P.inj_bstride + M.tile];
+  M.ie_end = P.inj_off[M.b * P.inj_bstride + M.tile + 1];
+  M.se_cur = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile] : 0;
+  M.se_end = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile + 1] : 0;
+  M.inj_z = M.ie_cur < M.ie_end ? P.inj[M.ie_cur].w : 0x7fffffff;
+  M.smp_z = M.se_cur < M.se_end ? P.smp4[M.se_cur].z : 0x7fffffff;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    M.Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    M.QS[i] = M.Q[i];
+  }
+  if (M.producer)
+    while (M.pq <= M.last_q && M.pq < S::NST - 4) M.issue();
+
+  // sequence q has queue centre index (q - 4) mod 9 = (q + 5) mod 9
+  int q = 0;
+  for (; q + 9 <= M.last_q + 1; q += 9) {
+    if (!M.template step<5>(q)) return;
+    if (!M.template step<6>(q + 1)) return;
+    if (!M.template step<7>(q + 2)) return;
+    if (!M.template step<8>(q + 3)) return;
+    if (!M.template step<0>(q + 4)) return;
+    if (!M.template step<1>(q + 5)) return;
+    if (!M.template step<2>(q + 6)) return;
+    if (!M.template step<3>(q + 7)) return;
+    if (!M.template step<4>(q + 8)) return;
+  }
+  const int rem = M.last_q + 1 - q;
+  if (rem > 0 && !M.template step<5>(q)) return;
+  if (rem > 1 && !M.template step<6>(q + 1)) return;
+  if (rem > 2 && !M.template step<7>(q + 2)) return;
+  if (rem > 3 && !M.template step<8>(q + 3)) return;
+  if (rem > 4 && !M.template step<0>(q + 4)) return;
+  if (rem > 5 && !M.template step<1>(q + 5)) return;
+  if (rem > 6 && !M.template step<2>(q + 6)) return;
+  if (rem > 7 && !M.template step<3>(q + 7)) return;
 }
 
-cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const Layout& L,
-                          const Coef& K, const StepParams& P, int B, cudaStream_t st) {
-  static bool attr_set[2] = {false, false};
+cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
+                          const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, int B,
+                          cudaStream_t st) {
   const int nty = (L.nyp + TY3 - 1) / TY3;
   dim3 grid(P.ntx, nty, B);
   if (adj) {
-    if (!attr_set[1]) {
-      cudaFuncSetAttribute(step3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem3D<true>::bytes);
-      attr_set[1] = true;
-    }
-    step3d_kernel<true><<<grid, NTHREADS, Smem3D<true>::bytes, st>>>(tm_halo, tm_plain, L, K, P);
+    const size_t bytes = Smem3D<true>::bytes(L.nzp);
+    cudaError_t e = cudaFuncSetAttribute(step3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    step3d_kernel<true><<<grid, NTHREADS, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
   } else {
-    if (!attr_set[0]) {
-      cudaFuncSetAttribute(step3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem3D<false>::bytes);
-      attr_set[0] = true;
-    }
-    step3d_kernel<false><<<grid, NTHREADS, Smem3D<false>::bytes, st>>>(tm_halo, tm_plain, L, K, P);
+    const size_t bytes = Smem3D<false>::bytes(L.nzp);
+    cudaError_t e = cudaFuncSetAttribute(step3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    step3d_kernel<false><<<grid, NTHREADS, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
   }
   return cudaGetLastError();
 }
