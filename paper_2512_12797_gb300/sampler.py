@@ -1,0 +1,205 @@
+"""Posterior samplers driven by the library's kernels.
+
+encoded_diffusion_sampler -- the decoupled, encoded-shot sampler of Sec. 2.3:
+    warm start at level t_start from the noised initial model (Sec. 2.2 and
+    3.2), then for every level t: predict the clean model x0^ (Sec. 2.3 (i)),
+    on guided levels run K clean-space Langevin steps with the unbiased
+    encoded gradient (Sec. 2.3 (ii), supergathers redrawn every step,
+    Sec. 3.2), and draw x_{t-1} from the DDPM posterior (Sec. 2.3 (iii)).
+plain_langevin -- the baseline: unadjusted Langevin on the full-shot
+    likelihood (every shot its own solve) plus a Gaussian smoothness prior.
+
+Both use the same Langevin kernel and the same reading of the step size "in
+physical units" (Sec. 2.3 (ii)): the gradient term is preconditioned per
+element by the running root-mean-square of that element's gradient (the
+diagonal preconditioner of preconditioned SGLD, Li et al. 2016, the Langevin
+counterpart of the Adam refinement of Sec. 3.2), so each step moves an
+element by about eta m/s; the independent noise has standard deviation nu
+m/s.
+
+The clean-model predictor here is the exact MMSE denoiser of a stationary
+Gaussian prior on the normalised model (diagonal in Fourier space).  It
+stands in for the trained network g_theta of Sec. 2.2, which this package
+does not provide; any callable (x_t, abar_t) -> x0^ can be passed instead.
+
+Cost is counted as eq. pde-count: one forward and one adjoint solve per
+supergather per gradient evaluation.
+"""
+import math
+import time
+
+import numpy as np
+
+from . import encode, langevin_step, renoise
+
+
+def ddpm_schedule(T=1000, beta1=1e-4, betaT=0.02):
+    """Linear beta schedule, cumulative alpha (Sec. 2.2; T = 1000, linear, Sec. 3.1)."""
+    beta = np.linspace(beta1, betaT, T)
+    return beta, np.cumprod(1.0 - beta)
+
+
+def normalize(v, vmin, vmax):
+    """Velocities to [-1, 1] (Sec. 2.2)."""
+    return 2.0 * (v - vmin) / (vmax - vmin) - 1.0
+
+
+def unnormalize(x, vmin, vmax):
+    return vmin + 0.5 * (x + 1.0) * (vmax - vmin)
+
+
+class GaussianPriorDenoiser:
+    """x0^ = E[x0 | x_t] for a stationary Gaussian prior x0 ~ N(m, C) on the
+    normalised model, C with spectrum amp^2 (1 + (k l)^2)^-2 (periodic
+    approximation).  With y = x_t / sqrt(abar_t) = x0 + sigma e,
+    sigma^2 = (1 - abar_t)/abar_t:  x0^ = m + F^-1[S / (S + sigma^2) F(y - m)]."""
+
+    def __init__(self, mean, corr_cells=6.0, amp=1.0):
+        import torch
+        self.mean = mean
+        shape = mean.shape[-2:]
+        kz = torch.fft.fftfreq(shape[0], device=mean.device) * 2 * math.pi
+        kx = torch.fft.rfftfreq(shape[1], device=mean.device) * 2 * math.pi
+        k2 = kz[:, None] ** 2 + kx[None, :] ** 2
+        # spectral density per Fourier mode, normalised so the pointwise variance is amp^2
+        S = (1.0 + k2 * corr_cells ** 2) ** -2
+        S = S / S.mean() * amp ** 2
+        self.S = S
+
+    def __call__(self, x_t, abar_t):
+        import torch
+        sig2 = (1.0 - abar_t) / abar_t
+        y = x_t / math.sqrt(abar_t) - self.mean
+        Y = torch.fft.rfft2(y)
+        return self.mean + torch.fft.irfft2(Y * (self.S / (self.S + sig2)), s=y.shape[-2:])
+
+
+def _rmse(v, truth):
+    return float(((v - truth) ** 2).mean().sqrt())
+
+
+def _rms_normalise(grad):
+    """Divide each sample's gradient by its root-mean-square value (in place)."""
+    g = grad.reshape(grad.shape[0], -1)
+    g.div_(g.pow(2).mean(dim=1).sqrt().clamp_min(1e-30)[:, None])
+
+
+class RMSPreconditioner:
+    """Diagonal preconditioner of preconditioned SGLD: g -> g / (sqrt(v) + eps),
+    v the exponential moving average of g^2 per element (in place on g)."""
+
+    def __init__(self, like, alpha=0.9, eps=1e-3):
+        import torch
+        self.v = torch.zeros_like(like)
+        self.alpha, self.eps, self.n = alpha, eps, 0
+
+    def __call__(self, g):
+        self.n += 1
+        self.v.mul_(self.alpha).addcmul_(g, g, value=1.0 - self.alpha)
+        vhat = self.v / (1.0 - self.alpha ** self.n)
+        g.div_(vhat.sqrt().add_(self.eps))
+
+
+def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, prior_lam=0.0, prior_mu=0.0,
+                   zref=None, seed=0, record_every=1, sg_sizes=None):
+    """Unadjusted Langevin on the full-shot likelihood (+ smoothness prior).
+
+    Every gradient evaluation solves each shot separately (N_s supergathers
+    of one shot, weight +1) -- or, with sg_sizes, uses the unbiased encoded
+    gradient of supergathers of those sizes, redrawn every step (Sec. 2.1,
+    3.2).  The RMS-normalised data gradient is combined with the gradient of
+    the smoothness prior lam/2 |grad(z - zref)|^2 + mu/2 |z - zref|^2.
+    Returns dict(rmse=[...], solves=[...], seconds, samples).
+    """
+    import torch
+    z = v0.clone()
+    ns = ctx.ns
+    nsamp = z.shape[0]
+    encoded = sg_sizes is not None
+    if not encoded:
+        perm = np.arange(ns, dtype=np.int32)
+        w = np.ones(ns, np.int8)
+        sg = [1] * ns
+    else:
+        sg = list(sg_sizes)
+    hist_r, hist_s = [_rmse(z.mean(0), truth)], [0]
+    zref = v0.mean(0) if zref is None else zref
+    grad = torch.empty_like(z)
+    precond = RMSPreconditioner(z)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solves = 0
+    for k in range(steps):
+        if encoded:
+            encs = [encode(seed * 7919 + i, k, ns) for i in range(nsamp)]
+            perm = np.stack([e[0] for e in encs])
+            w = np.stack([e[1] for e in encs])
+        ctx.gradient(z, perm, w, sg, d_obs, sigma, scale=0.0 if encoded else 1.0, grad=grad)
+        _rms_normalise(grad)
+        if prior_lam > 0 or prior_mu > 0:
+            ctx.smooth_prior_grad(z, zref.contiguous(), prior_lam, prior_mu, grad)
+        precond(grad)
+        langevin_step(z, grad, eta, nu, vmin, vmax, seed, k)
+        solves += 2 * len(sg) * nsamp
+        if (k + 1) % record_every == 0:
+            hist_r.append(_rmse(z.mean(0), truth))
+            hist_s.append(solves)
+    torch.cuda.synchronize()
+    return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0, "samples": z}
+
+
+def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_start, stride, K, eta, nu, vmin, vmax,
+                              sigma, denoiser=None, seed=0, renoise_on=True):
+    """Decoupled encoded-shot diffusion sampler (Sec. 2.3, Algorithm table).
+
+    v_init: [nz, nx] initial model (m/s).  Starts from level t_start with
+    x_t = sqrt(abar) x_init + sqrt(1 - abar) eps; guided levels are every
+    `stride`-th level, each with K Langevin steps on the encoded likelihood
+    with the given supergather sizes.  Returns dict(rmse, solves, seconds,
+    samples) with the posterior-mean RMSE after every guided level.
+    """
+    import torch
+    beta, abar = ddpm_schedule()
+    dev = v_init.device
+    x_init = normalize(v_init, vmin, vmax)
+    if denoiser is None:
+        denoiser = GaussianPriorDenoiser(x_init)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    t = t_start
+    x_t = (math.sqrt(abar[t - 1]) * x_init[None] +
+           math.sqrt(1 - abar[t - 1]) * torch.randn((nsamp,) + tuple(v_init.shape), device=dev, generator=gen))
+    x_t = x_t.contiguous()
+    grad = torch.empty_like(x_t)
+    precond = RMSPreconditioner(x_t)
+    hist_r, hist_s = [_rmse(v_init, truth)], [0]
+    solves = 0
+    it = 0
+    nsg = len(sg_sizes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    z = None
+    for t in range(t_start, 0, -1):
+        x0 = denoiser(x_t, abar[t - 1]).clamp(-1.0, 1.0)
+        if t % stride == 0 or t == 1:
+            z = unnormalize(x0, vmin, vmax).contiguous()
+            for k in range(K):
+                encs = [encode(seed * 7919 + s, it, ctx.ns) for s in range(nsamp)]
+                perm = np.stack([e[0] for e in encs])
+                w = np.stack([e[1] for e in encs])
+                ctx.gradient(z, perm, w, sg_sizes, d_obs, sigma, grad=grad)
+                _rms_normalise(grad)
+                precond(grad)
+                langevin_step(z, grad, eta, nu, vmin, vmax, seed + 1, it)
+                solves += 2 * nsg * nsamp
+                it += 1
+            x0 = normalize(z, vmin, vmax).contiguous()
+            hist_r.append(_rmse(z.mean(0), truth))
+            hist_s.append(solves)
+        if t > 1:
+            if renoise_on:
+                x_t = renoise(x_t.contiguous(), x0.contiguous(), abar[t - 1], abar[t - 2], beta[t - 1], seed + 2, t)
+            else:
+                x_t = (math.sqrt(abar[t - 2]) * x0).contiguous()
+    torch.cuda.synchronize()
+    return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0,
+            "samples": unnormalize(x0, vmin, vmax)}
