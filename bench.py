@@ -287,24 +287,25 @@ def native_arm(args):
     h2d = vel_h.numel() * 4 + dobs_h.numel() * 4
     d2h = out_h.numel() * 4 + nsamp * 8
 
-    # roofline of the dominant step kernel from the per-phase events
+    # roofline of the dominant step kernel from the per-phase events.  In 2D one
+    # launch runs all steps of a phase (forward: nt steps; adjoint: the steps of a
+    # checkpoint segment), in 3D every step is a launch; both are charged per step.
     bpu = bytes_per_update(nsg, w.ndim)
     n = args.steps
     nchunks = (nsamp + plan["samples_per_chunk"] - 1) // plan["samples_per_chunk"]
-    fwd_launch_ms = phase_ms[0] / max(phase_launch[0] - nchunks * n, 1)  # phase 0 also holds one expand per chunk
-    adj_phase_launch = phase_launch[2]
-    adj_launch_ms = phase_ms[2] / max(adj_phase_launch, 1)
-    per_launch_pts = w.padded_points * plan["samples_per_chunk"] * nsg  # wavefields of one launch
-    # the adjoint phase also holds the recompute (forward) launches: split it by
-    # charging them the forward kernel's average launch time
-    rec_launches = adj_phase_launch - w.nt * nchunks * n
-    adj_only_ms = phase_ms[2] - max(rec_launches, 0) * fwd_launch_ms
-    adj_launch_ms = adj_only_ms / max(adj_phase_launch - max(rec_launches, 0), 1)
+    fwd_steps = w.nt * nchunks * n
+    rec_steps = plan["recomputed_steps"] * nchunks * n
+    fwd_step_ms = phase_ms[0] / max(fwd_steps, 1)  # phase 0 also holds one expand launch per chunk
+    # the adjoint phase also holds the recomputed forward steps: charge them the
+    # forward steps' average time
+    adj_only_ms = phase_ms[2] - rec_steps * fwd_step_ms
+    adj_step_ms = adj_only_ms / max(w.nt * nchunks * n, 1)
+    per_step_pts = w.padded_points * plan["samples_per_chunk"] * nsg  # wavefields of one step
     kd = "3d" if w.ndim == 3 else "2d"
     kern = {
-        "step%s_kernel<ADJ>" % kd: {"ms": adj_launch_ms, "bytes": bpu["adjoint"] * per_launch_pts,
+        "step%s_kernel<ADJ>" % kd: {"ms": adj_step_ms, "bytes": bpu["adjoint"] * per_step_pts,
                                     "share": adj_only_ms / max(phase_ms.sum(), 1e-9)},
-        "step%s_kernel<FWD>" % kd: {"ms": fwd_launch_ms, "bytes": bpu["forward"] * per_launch_pts,
+        "step%s_kernel<FWD>" % kd: {"ms": fwd_step_ms, "bytes": bpu["forward"] * per_step_pts,
                                     "share": (phase_ms[0] + phase_ms[2] - adj_only_ms) / max(phase_ms.sum(), 1e-9)},
     }
     dom = max(kern, key=lambda k: kern[k]["share"])
@@ -340,9 +341,11 @@ def native_arm(args):
                         "frac": achieved / peak, "traffic": None,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
                         "bytes_per_update": bpu["adjoint" if "ADJ" in dom else "forward"],
-                        "avg_launch_ms": kern[dom]["ms"],
+                        "avg_step_ms": kern[dom]["ms"],
+                        "steps_per_launch": ({"forward": w.nt, "adjoint": min(plan["segment_len"], w.nt)}
+                                             if w.ndim == 2 else {"forward": 1, "adjoint": 1}),
                         "other_kernel": {"name": other, "achieved": other_gbs, "frac": other_gbs / peak,
-                                         "avg_launch_ms": kern[other]["ms"]}},
+                                         "avg_step_ms": kern[other]["ms"]}},
            "phase_ms_per_step": {"forward": phase_ms[0] / n, "residual": phase_ms[1] / n,
                                  "adjoint": phase_ms[2] / n, "finalize": phase_ms[3] / n},
            "clocks": clocks, "cpu_baseline": cpu}

@@ -107,6 +107,8 @@ bool make_plan(int nt, long long avail, Plan* out) {
   return found;
 }
 
+constexpr int kTuneSteps = 6;  // steps per autotuner timing launch
+
 struct Entry {  // a point on the padded grid with a record column and amplitude
   int z, y, x, col;
   float amp;
@@ -164,6 +166,16 @@ struct fwi_ctx {
   float tune_ms[2][8] = {};
   int* zero_off = nullptr;  // [ntiles+1] zeros: "no points in any tile"
   float* gtab = nullptr;    // gamma*dt per axis: z [nzp], y [nyp], x [nxp]
+  // step descriptors of the current call, in launch order (device, pinned
+  // staging, host copy), the autotuner's steps, and the per-item progress
+  // flags of the multi-step 2D launches
+  StepDesc* desc = nullptr;
+  StepDesc* hdesc = nullptr;
+  size_t desc_cap = 0;
+  cudaEvent_t ev_desc = nullptr;
+  std::vector<StepDesc> descs;
+  StepDesc* tdesc = nullptr;
+  int* done = nullptr;  // [max_B * ntiles]
 };
 
 namespace {
@@ -460,10 +472,54 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
   return P;
 }
 
-cudaError_t launch_step(fwi_ctx* C, bool adj, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
-                        const CUtensorMap& tg, const StepParams& P, int nsamp, int B, cudaStream_t st) {
-  if (C->L.ndim == 3) return launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st);
-  return launch_step2d(adj, C->var[adj ? 1 : 0], th, tp, tc, C->L, C->K, P, nsamp, st);
+// Steps descs[off, off + n) of the current call: one multi-step launch in 2D
+// (progress flags zeroed first), one launch per step in 3D.
+int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int B, const CUtensorMap& th,
+              const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, cudaStream_t st,
+              long long* launches) {
+  if (n <= 0) return FWI_OK;
+  if (C->L.ndim == 3) {
+    for (int i = 0; i < n; i++) {
+      const StepDesc& d = C->descs[off + i];
+      P.s_cur = d.cur;
+      P.s_prev = d.prev;
+      P.s_out = d.out;
+      P.s_snap = d.snap;
+      P.t = d.t;
+      CK(launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st));
+    }
+    *launches += n;
+    return FWI_OK;
+  }
+  P.steps = C->desc + off;
+  P.nsteps = n;
+  P.done = C->done;
+  CK(cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st));
+  CK(launch_step2d(adj, C->var[adj ? 1 : 0], th, tp, tc, C->L, C->K, P, nsamp, st));
+  *launches += 1;
+  return FWI_OK;
+}
+
+// Copies the call's step descriptors (C->descs) to the device.
+int upload_descs(fwi_ctx* C, cudaStream_t st) {
+  const size_t n = C->descs.size();
+  if (n > C->desc_cap) return FWI_ERR_ARG;
+  CK(cudaEventSynchronize(C->ev_desc));  // the previous copy out of the staging buffer is done
+  memcpy(C->hdesc, C->descs.data(), n * sizeof(StepDesc));
+  CK(cudaMemcpyAsync(C->desc, C->hdesc, n * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(C->ev_desc, st));
+  return FWI_OK;
+}
+
+StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
+  StepDesc d;
+  d.cur = cur;
+  d.prev = prev;
+  d.out = out;
+  d.snap = snap;
+  d.t = t;
+  d.pad[0] = d.pad[1] = d.pad[2] = 0;
+  return d;
 }
 
 // Autotuner: time every compiled variant of the forward and adjoint step
@@ -493,23 +549,29 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtens
     P.inj_bstride = 0;
     P.inj = C->rec_inj;
     P.series = C->wav;
-    P.s_cur = P.s_prev = P.s_snap = Plan::ZERO;
-    P.s_out = Plan::RING;
+    P.steps = C->tdesc;  // zero slot in, one ring slot out, every step
+    P.nsteps = kTuneSteps;
+    P.done = C->done;
+    const size_t done_bytes = (size_t)nsamp * C->ntiles * 4;
     int best = -1;
     float best_ms = 1e30f;
     for (int v = 0; v < nv && v < 8; v++) {
       C->tune_ms[adj][v] = -1.f;
+      CK(cudaMemsetAsync(C->done, 0, done_bytes, st));
       if (launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st) != cudaSuccess) {
         cudaGetLastError();  // variant does not fit this device: skip it
         continue;
       }
       CK(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; r++) CK(launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st));
+      for (int r = 0; r < 3; r++) {
+        CK(cudaMemsetAsync(C->done, 0, done_bytes, st));
+        CK(launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st));
+      }
       CK(cudaEventRecord(e1, st));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      C->tune_ms[adj][v] = ms / 3.f;
+      C->tune_ms[adj][v] = ms / (3.f * kTuneSteps);  // per step
       if (ms < best_ms) {
         best_ms = ms;
         best = v;
@@ -689,9 +751,27 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
-  if (cudaEventCreateWithFlags(&C->ev_list, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&C->ev_list, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&C->ev_desc, cudaEventDisableTiming) != cudaSuccess) {
     fwi_destroy(C);
     return FWI_ERR_CUDA;
+  }
+  // step descriptors: forward, recomputed and adjoint steps of one call
+  C->desc_cap = 3 * (size_t)g->nt + 16;
+  if (!alloc((void**)&C->desc, C->desc_cap * sizeof(StepDesc)) ||
+      cudaHostAlloc((void**)&C->hdesc, C->desc_cap * sizeof(StepDesc), cudaHostAllocDefault) != cudaSuccess ||
+      !alloc((void**)&C->tdesc, kTuneSteps * sizeof(StepDesc)) ||
+      !alloc((void**)&C->done, (size_t)B * C->ntiles * 4)) {
+    fwi_destroy(C);
+    return FWI_ERR_OOM;
+  }
+  {
+    std::vector<StepDesc> td(kTuneSteps);
+    for (int i = 0; i < kTuneSteps; i++) td[i] = StepDesc{Plan::ZERO, Plan::ZERO, Plan::RING, Plan::ZERO, 0, {0, 0, 0}};
+    if (cudaMemcpy(C->tdesc, td.data(), td.size() * sizeof(StepDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+      fwi_destroy(C);
+      return FWI_ERR_CUDA;
+    }
   }
   for (int i = 0; i < 5; i++)
     if (cudaEventCreate(&C->ev[i]) != cudaSuccess) {
@@ -740,15 +820,32 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->dlist);
   cudaFree(C->zero_off);
   cudaFree(C->gtab);
+  cudaFree(C->desc);
+  cudaFree(C->tdesc);
+  cudaFree(C->done);
   if (C->hlist) cudaFreeHost(C->hlist);
+  if (C->hdesc) cudaFreeHost(C->hdesc);
   if (C->ev_list) cudaEventDestroy(C->ev_list);
+  if (C->ev_desc) cudaEventDestroy(C->ev_desc);
   for (int i = 0; i < 5; i++)
     if (C->ev[i]) cudaEventDestroy(C->ev[i]);
   delete C;
 }
 
+// Forward steps 0..nt-1 with the slots of the checkpoint plan, or of a
+// three-slot ring when no snapshots are kept.
+static void append_forward_descs(fwi_ctx* C, const Plan* plan) {
+  for (int n = 0; n < C->g.nt; n++) {
+    if (plan)
+      C->descs.push_back(make_desc(plan->fslot(n), plan->fslot(n - 1), plan->fslot(n + 1), Plan::ZERO, n));
+    else
+      C->descs.push_back(make_desc(n <= 0 ? 0 : 1 + n % 3, n - 1 <= 0 ? 0 : 1 + (n - 1) % 3, 1 + (n + 1) % 3,
+                                   Plan::ZERO, n));
+  }
+}
+
 static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const CUtensorMap& th,
-                            const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, const Plan* plan,
+                            const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, int desc_off,
                             float* dout, cudaStream_t st) {
   const int B = nsamp * nsg;
   StepParams P = base_params(C, B, nsg);
@@ -767,21 +864,7 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
   P.smp_out = dout;
   P.smp_bstride_out = (long long)C->g.nt * C->nr;
   P.smp_ld = C->nr;
-  for (int n = 0; n < C->g.nt; n++) {
-    if (plan) {
-      P.s_cur = plan->fslot(n);
-      P.s_prev = plan->fslot(n - 1);
-      P.s_out = plan->fslot(n + 1);
-    } else {
-      P.s_cur = n <= 0 ? 0 : 1 + n % 3;
-      P.s_prev = n - 1 <= 0 ? 0 : 1 + (n - 1) % 3;
-      P.s_out = 1 + (n + 1) % 3;
-    }
-    P.t = n;
-    CK(launch_step(C, false, th, tp, tc, tg, P, nsamp, B, st));
-  }
-  C->launches[0] += C->g.nt;
-  return FWI_OK;
+  return run_steps(C, false, P, desc_off, C->g.nt, nsamp, B, th, tp, tc, tg, st, &C->launches[0]);
 }
 
 int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
@@ -803,8 +886,11 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   for (int i = 0; i < 4; i++) C->launches[i] = 0;
   C->last_was_gradient = false;
   prof_mark(C, 0, st);
+  C->descs.clear();
+  append_forward_descs(C, nullptr);
+  if ((rc = upload_descs(C, st)) != FWI_OK) return rc;
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, nullptr, d_pred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, d_pred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
   prof_mark(C, 2, st);
   prof_mark(C, 3, st);
@@ -835,11 +921,30 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
 
   prof_mark(C, 0, st);
+  // step descriptors of the whole chunk: forward, then per segment j (last
+  // first) the recomputed forward steps and the adjoint steps
+  C->descs.clear();
+  append_forward_descs(C, &plan);
+  std::vector<int> rc_off(plan.jL + 1), rc_n(plan.jL + 1), ad_off(plan.jL + 1), ad_n(plan.jL + 1);
+  for (int j = plan.jL; j >= 0; j--) {
+    const int m0 = j * plan.K, m1 = std::min((j + 1) * plan.K, nt);  // snapshots m0..m1-1
+    rc_off[j] = (int)C->descs.size();
+    if (j < plan.jL)
+      for (int n = m0; n <= m1 - 2; n++)
+        C->descs.push_back(make_desc(plan.rslot(j, n), plan.rslot(j, n - 1), plan.rslot(j, n + 1), Plan::ZERO, n));
+    rc_n[j] = (int)C->descs.size() - rc_off[j];
+    ad_off[j] = (int)C->descs.size();
+    for (int k = m1; k >= m0 + 1; k--)
+      C->descs.push_back(make_desc(plan.qslot(k + 1), plan.qslot(k + 2), plan.qslot(k), plan.snap(j, k - 1), k - 1));
+    ad_n[j] = (int)C->descs.size() - ad_off[j];
+  }
+  if ((rc = upload_descs(C, st)) != FWI_OK) return rc;
+
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
   C->launches[0] += 1;
   const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
   CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, &plan, C->dpred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
   // residual (rhat overwrites dpred) and misfit
@@ -876,26 +981,10 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   A.smp_ld = C->Emax;
   long long adj_launch = 0;
   for (int j = plan.jL; j >= 0; j--) {
-    const int m0 = j * plan.K, m1 = std::min((j + 1) * plan.K, nt);  // snapshots m0..m1-1
-    if (j < plan.jL) {
-      for (int n = m0; n <= m1 - 2; n++) {
-        F.s_cur = plan.rslot(j, n);
-        F.s_prev = plan.rslot(j, n - 1);
-        F.s_out = plan.rslot(j, n + 1);
-        F.t = n;
-        CK(launch_step(C, false, th, tp, tc, tg, F, nsamp, B, st));
-        adj_launch++;
-      }
-    }
-    for (int k = m1; k >= m0 + 1; k--) {
-      A.s_cur = plan.qslot(k + 1);
-      A.s_prev = plan.qslot(k + 2);
-      A.s_out = plan.qslot(k);
-      A.s_snap = plan.snap(j, k - 1);
-      A.t = k - 1;
-      CK(launch_step(C, true, th, tp, tc, tg, A, nsamp, B, st));
-      adj_launch++;
-    }
+    if ((rc = run_steps(C, false, F, rc_off[j], rc_n[j], nsamp, B, th, tp, tc, tg, st, &adj_launch)) != FWI_OK)
+      return rc;
+    if ((rc = run_steps(C, true, A, ad_off[j], ad_n[j], nsamp, B, th, tp, tc, tg, st, &adj_launch)) != FWI_OK)
+      return rc;
   }
   C->launches[2] += adj_launch;
   prof_mark(C, 3, st);

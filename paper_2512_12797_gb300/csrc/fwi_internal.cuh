@@ -43,8 +43,16 @@ struct Coef {
   float inv_nb;               // 1 / nb (0 when nb == 0)
 };
 
+// Slots and record time of one step of a multi-step launch.
+struct StepDesc {
+  int cur, prev, out, snap;  // pool slots of the stepped level, the older level, the output, the snapshot
+  int t;                     // record time index of the step's injection and sampling
+  int pad[3];
+};
+
 // One time step of the forward recursion (FWD) or of the adjoint recursion
-// with the imaging condition (ADJ) over all wavefields of a call.
+// with the imaging condition (ADJ) over all wavefields of a call; the 2D
+// kernels run nsteps such steps, described by steps[], in one launch.
 struct StepParams {
   float* pool;              // slot pool base
   long long slot_elems;     // B * field floats per slot
@@ -65,9 +73,15 @@ struct StepParams {
   const int4* smp4;         // {local, col, z, 0}                (3D; inj .w holds z)
   float* smp_out; long long smp_bstride_out; int smp_ld;
   int* status;
+  // multi-step launches (2D): step descriptors and per-item progress flags
+  // (item = tile of one sample, flag = steps completed; zero at launch)
+  const StepDesc* steps; int nsteps;
+  int* done;
 };
 
 // Host-side launchers (stencil.cu)
+// Runs P.nsteps steps of all nsamp * P.nsg wavefields in one cooperative launch;
+// P.done must hold nsamp * P.ntiles zeroed ints.
 cudaError_t launch_step2d(bool adj, int variant, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
                           const CUtensorMap& tm_c, const Layout& L, const Coef& K, const StepParams& P, int nsamp,
                           cudaStream_t st);
@@ -151,6 +165,79 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
   }
   return true;
+}
+
+// Shared-memory fetch-add with acquire-release semantics at CTA scope.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+// Wait with a suspend-time hint (ns) between hardware polls.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait that also gives up when another warp of the CTA has set the
+// shared abort word (after its own wait ran out).
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity, int* status,
+                                                    volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_hint(bar, parity, 1000000u)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(status, 0, (int)FWI_ERR_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Memory-model helpers for the cross-CTA progress flags.
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(int* p, int v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta_shared(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_cta_shared(int* p, int v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Register reallocation between warpgroups (all warps of a warpgroup execute it).
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
 }
 
 // TMA tiled loads into shared memory, completion counted on an mbarrier.

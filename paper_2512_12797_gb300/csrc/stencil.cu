@@ -1,7 +1,7 @@
-// stencil.cu -- time-step kernels of the damped 8th-order acoustic recursion
-// and of its exact discrete adjoint with the imaging condition.
+// stencil.cu -- multi-step kernels of the damped 8th-order acoustic recursion
+// (2D) and of its exact discrete adjoint with the imaging condition.
 //
-// Forward step (one launch per time step, all wavefields of the call):
+// Forward step:
 //     p^{n+1} = p^n + b (p^n - p^{n-1}) + cc (L p^n + s^n)
 // with b = (1 - gamma dt)/(1 + gamma dt), cc = v^2 dt^2/(1 + gamma dt).  This is
 // the damped leapfrog p^{n+1} = [2p^n - (1-gamma dt)p^{n-1} + c(Lp^n + s^n)]/(1+gamma dt)
@@ -19,32 +19,61 @@
 // accumulated here as G += q^k * L p^{k-1} (the source term is added from
 // source-point samples after the time loop).
 //
-// Tiling: work items are 128 x 32 (x, z) tiles of one posterior sample; a
-// CTA processes an item for all of the sample's supergathers in a row, so the
-// velocity coefficients and the imaging accumulator are loaded once per tile
-// and reused across them.  Halo tiles (136 x 40) of p^n (and of the snapshot
-// p^{k-1} in the adjoint) and the tile of p^{n-1} are fetched by TMA into a
-// multi-stage shared-memory ring.  Each thread computes a 4 (x) x R (z) block:
-// x-neighbours from two float4 shared loads per row, z-neighbours from an
-// (R+8)-row float4 column window held in registers.
+// One cooperative launch runs many time steps.  Work items are 128 x 32 (x, z)
+// tiles of one posterior sample; CTA c owns items c, c + G, c + 2G, ... in
+// every step and processes each for all of the sample's supergathers in a row.
+// Steps are chained tile by tile instead of by kernel boundaries: an item's
+// loads for step n wait until the 3 x 3 tile neighbourhood has finished step
+// n-1 (per-item progress flags in global memory).  Because a level's slot is
+// reused at the earliest three steps later, that single condition also covers
+// the write-after-read hazards of the slot ring.
+//
+// Each CTA is warp-specialised: two consumer warpgroups (8 warps, 4 rows x 4
+// columns per thread) compute, and a producer warpgroup runs
+//   warp 8  -- the TMA ring: halo tile of the stepped level (and of the
+//              snapshot in the adjoint), plain tile of the older level, the cc
+//              tile once per item; waits for the progress flags first;
+//   warp 9  -- the point lists of each iteration (injection entries with their
+//              scaled series values, sampling entries), copied into the stage
+//              so that no consumer waits on a dependent global load;
+//   warp 10 -- publishes an item's progress flag once all consumer warps have
+//              stored its outputs;
+//   warp 11 -- polls the progress flags of upcoming items ahead of warp 8 and
+//              counts the items whose neighbourhood is ready.
+// setmaxnreg moves registers from the producer to the consumer warpgroups.
 #include "fwi_internal.cuh"
 
 namespace fwi {
 
-// One ring stage: halo tile of the field being stepped, plain tile of the older
-// level, [halo tile of the snapshot], plain tile of cc (filled for the first
-// supergather of a work item), and the four point-list offsets of the
-// iteration (inj begin/end, smp begin/end).  Every part starts on 128 bytes.
+constexpr int R2D = 4;                       // rows per consumer thread
+constexpr int NCW2D = TZ / R2D;              // consumer warps (8)
+constexpr int NTHREADS2D = 32 * NCW2D + 128;  // + producer warpgroup
+constexpr int PCAP = 256;                    // point-list entries staged per stage and list
+constexpr int WDONE = 8;                     // item-completion counters (ring)
+constexpr int REG_LAUNCH = 168, REG_PRODUCER = 72, REG_CONSUMER = 216;
+static_assert(128 * REG_PRODUCER + 32 * NCW2D * REG_CONSUMER <= NTHREADS2D * REG_LAUNCH,
+              "register split exceeds the launch allocation");
+
+// One ring stage: halo tile of the stepped level, plain tile of the older
+// level, [halo tile of the snapshot], and the iteration's point lists:
+//   PTS[0..5]   = staged injection count, staged sampling count, global
+//                 injection range [begin, end), global sampling range [begin, end)
+//   PTS[32 ..]  = injection local index [PCAP], injection value [PCAP],
+//                 sampling local index [PCAP], sampling record column [PCAP].
+// Two cc tiles follow the stages.  Every part starts on 128 bytes.
 template <bool ADJ, int NS>
 struct Smem2D {
   static constexpr int IN = HZ * HX;   // floats in one halo tile
   static constexpr int PV = TZ * TX;   // floats in one plain tile
+  static constexpr int PTS = 32 + 4 * PCAP;
   static constexpr int OFF_SNAP = IN + PV;
-  static constexpr int OFF_C = OFF_SNAP + (ADJ ? IN : 0);
-  static constexpr int OFF_IDX = OFF_C + PV;
-  static constexpr int STAGE = OFF_IDX + 32;
-  static constexpr int nfloat = NS * STAGE;
-  static constexpr int bytes = nfloat * 4 + 2 * NS * 8;  // + full and empty barriers
+  static constexpr int OFF_PTS = OFF_SNAP + (ADJ ? IN : 0);
+  static constexpr int STAGE = OFF_PTS + PTS;
+  static constexpr int OFF_C = NS * STAGE;
+  static constexpr int nfloat = OFF_C + 2 * PV;
+  static constexpr int nbar = 2 * NS + 4;  // full[NS], empty[NS], cfull[2], cempty[2]
+  static constexpr int bytes = nfloat * 4 + nbar * 8 + (WDONE + 4) * 4;
+  static_assert((STAGE * 4) % 128 == 0 && (PTS * 4) % 128 == 0, "stage parts must stay 128-byte aligned");
 };
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -94,97 +123,284 @@ __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, i
   }
 }
 
-// Persistent kernel with per-stage full/empty mbarriers.  One CTA per SM walks
-// its work items (item = tile of one sample) and, inside each, the sample's
-// supergathers; iteration number it counts (item, supergather) pairs.  Every
-// warp waits on the stage's "full" mbarrier (TMA transaction count plus one
-// arrival from the cp.async copy of the iteration's point-list offsets),
-// computes its rows and releases the stage on its "empty" mbarrier (one
-// arrival per warp).  Lane 0 of the last warp is also the producer: it refills
-// a stage as soon as every warp has released it, testing the empty barrier
-// without blocking, and blocks only when the iteration its own warp needs next
-// has not been issued yet, so loads run up to NS-1 iterations ahead with no
-// CTA-wide barrier in the loop.  The cc tile of an item travels with the
-// item's first supergather; sponge coefficients come from per-axis gamma*dt
-// tables.  Source injection and receiver sampling are staged by each warp in
-// its own rows of the stage's p^{n-1} buffer, which it has already consumed.
-template <bool ADJ, int NS, int R, bool ISO>
-__global__ void __launch_bounds__(32 * (TZ / R), 1)
+// Bounded poll of the progress flags of the 3 x 3 tile neighbourhood of item
+// (s, tile) until each has completed `need` steps; then acquire-orders the
+// neighbours' stores before the TMA loads that follow.  Gives up on timeout,
+// on the CTA's abort word, or when another CTA has recorded an error.
+__device__ __noinline__ bool wait_neighbours(const StepParams& P, int s, int tile, int need,
+                                             volatile int* abort_flag) {
+  const int tx = tile % P.ntx, tz = tile / P.ntx, ntz = P.ntiles / P.ntx;
+  const int* base = P.done + (long long)s * P.ntiles;
+  const int z_lo = max(tz - 1, 0), z_hi = min(tz + 1, ntz - 1);
+  const int x_lo = max(tx - 1, 0), x_hi = min(tx + 1, P.ntx - 1);
+  const long long t0 = clock64();
+  for (;;) {
+    int lo = need;
+    for (int z = z_lo; z <= z_hi; z++)
+      for (int x = x_lo; x <= x_hi; x++) lo = min(lo, ld_relaxed_gpu(base + z * P.ntx + x));
+    if (lo >= need) break;
+    if (*abort_flag || ld_relaxed_gpu(P.status) != 0) {
+      *abort_flag = 1;
+      return false;
+    }
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(P.status, 0, (int)FWI_ERR_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+    __nanosleep(128);
+  }
+  fence_acq_rel_gpu();
+  fence_proxy_async_global();
+  return true;
+}
+
+// After an abort: bounded wait for the copies this thread issued into the
+// last `n` stages (or cc buffers) so that none lands after the CTA exits.
+__device__ __forceinline__ void drain(uint64_t* bars, int nbars, int issued, int n) {
+  for (int i = max(issued - n, 0); i < issued; i++) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&bars[i % nbars], (uint32_t)((i / nbars) & 1)))
+      if (clock64() - t0 > (1LL << 24)) break;
+  }
+}
+
+// Warp 8, lane 0: TMA ring.  Iteration m = ((step n, item k), supergather j)
+// fills stage m % NS; the cc tile of (n, k) goes to buffer ic & 1.
+template <bool ADJ, int NS>
+__device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CUtensorMap* tm_plain,
+                                            const CUtensorMap* tm_c, const StepParams& P, float* sm,
+                                            uint64_t* full, uint64_t* empty, uint64_t* cfull, uint64_t* cempty,
+                                            int* deps_ok, int my_items, volatile int* abort_flag) {
+  using S = Smem2D<ADJ, NS>;
+  constexpr uint32_t TX_BYTES = (S::IN + S::PV + (ADJ ? S::IN : 0)) * 4;
+  const int G = gridDim.x, nsg = P.nsg;
+  int m = 0, ic = 0;
+  for (int n = 0; n < P.nsteps; n++) {
+    const int4 d = __ldg(reinterpret_cast<const int4*>(P.steps + n));  // cur, prev, out, snap
+    for (int k = 0; k < my_items; k++, ic++) {
+      const int item = (int)blockIdx.x + k * G;
+      const int s = item / P.ntiles, tile = item - s * P.ntiles;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      if (n > 0) {  // neighbourhood of (n, k) ready: counted by warp 11
+        const long long t0 = clock64();
+        while (ld_acquire_cta_shared(deps_ok) <= ic) {
+          if (*abort_flag) goto aborted;
+          if (clock64() - t0 > WAIT_CYCLES) {
+            atomicCAS(P.status, 0, (int)FWI_ERR_TIMEOUT);
+            *abort_flag = 1;
+            goto aborted;
+          }
+          __nanosleep(32);
+        }
+        fence_proxy_async_global();
+      }
+      {
+        const int cs = ic & 1;
+        if (ic >= 2 && !mbar_wait_abortable(&cempty[cs], (uint32_t)(((ic >> 1) - 1) & 1), P.status, abort_flag))
+          goto aborted;
+        mbar_arrive_expect_tx(&cfull[cs], S::PV * 4);
+        tma_load_3d(sm + S::OFF_C + cs * S::PV, tm_c, x0 + HALO, z0 + HALO, s, &cfull[cs]);
+      }
+      for (int j = 0; j < nsg; j++, m++) {
+        const int st = m % NS;
+        if (m >= NS && !mbar_wait_abortable(&empty[st], (uint32_t)((m / NS - 1) & 1), P.status, abort_flag))
+          goto aborted;
+        const int b = s * nsg + j;
+        float* base = sm + st * S::STAGE;
+        mbar_arrive_expect_tx(&full[st], TX_BYTES);
+        tma_load_4d(base, tm_halo, x0, z0, b, d.x, &full[st]);
+        tma_load_4d(base + S::IN, tm_plain, x0 + HALO, z0 + HALO, b, d.y, &full[st]);
+        if (ADJ) tma_load_4d(base + S::OFF_SNAP, tm_halo, x0, z0, b, d.w, &full[st]);
+      }
+    }
+  }
+  return;
+aborted:
+  drain(full, NS, m, NS);
+  drain(cfull, 2, ic, 2);
+}
+
+// Warp 9: point lists.  For every iteration the warp copies the injection
+// entries of (wavefield, tile) with their values cc * amp * series[t] and the
+// sampling entries into the stage's PTS block (at most PCAP of each; the
+// consumers take any rest from global memory), then arrives on the stage's
+// full barrier.  Offsets of an item's supergathers are loaded one item ahead.
+template <bool ADJ, int NS>
+__device__ __forceinline__ void produce_points(const Layout& L, const StepParams& P, float* sm, uint64_t* full,
+                                               uint64_t* empty, int my_items, int lane,
+                                               volatile int* abort_flag) {
+  using S = Smem2D<ADJ, NS>;
+  const int G = gridDim.x, nsg = P.nsg;
+  const bool has_smp = P.smp != nullptr;
+  // offsets of supergather j0 + lane of item k: inj [a0, a1), smp [b0, b1)
+  auto load_offsets = [&](int k, int j0, int& a0, int& a1, int& b0, int& b1) {
+    const int item = (int)blockIdx.x + k * G;
+    const int s = item / P.ntiles, tile = item - s * P.ntiles;
+    a0 = a1 = b0 = b1 = 0;
+    if (j0 + lane < nsg) {
+      const int b = s * nsg + j0 + lane;
+      const int* io = P.inj_off + (long long)b * P.inj_bstride + tile;
+      a0 = __ldg(io);
+      a1 = __ldg(io + 1);
+      if (has_smp) {
+        const int* so = P.smp_off + (long long)b * P.smp_bstride + tile;
+        b0 = __ldg(so);
+        b1 = __ldg(so + 1);
+      }
+    }
+  };
+  int na0, na1, nb0, nb1;
+  load_offsets(0, 0, na0, na1, nb0, nb1);
+  int m = 0;
+  for (int n = 0; n < P.nsteps; n++) {
+    const int t = __ldg(&P.steps[n].t);
+    for (int k = 0; k < my_items; k++) {
+      const int item = (int)blockIdx.x + k * G;
+      const int s = item / P.ntiles, tile = item - s * P.ntiles;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      const float* cs = P.c + (long long)s * L.field;
+      for (int j0 = 0; j0 < nsg; j0 += 32) {
+        int a0 = na0, a1 = na1, b0 = nb0, b1 = nb1;
+        // prefetch the next chunk (or the next item's first chunk)
+        if (j0 + 32 < nsg)
+          load_offsets(k, j0 + 32, na0, na1, nb0, nb1);
+        else
+          load_offsets(k + 1 < my_items ? k + 1 : 0, 0, na0, na1, nb0, nb1);
+        const int jn = min(32, nsg - j0);
+        for (int jj = 0; jj < jn; jj++, m++) {
+          const int io0 = __shfl_sync(0xffffffffu, a0, jj), io1 = __shfl_sync(0xffffffffu, a1, jj);
+          const int so0 = __shfl_sync(0xffffffffu, b0, jj), so1 = __shfl_sync(0xffffffffu, b1, jj);
+          const int st = m % NS;
+          int ok = 1;
+          if (m >= NS && lane == 0)
+            ok = mbar_wait_abortable(&empty[st], (uint32_t)((m / NS - 1) & 1), P.status, abort_flag);
+          if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+          int* pts = reinterpret_cast<int*>(sm + st * S::STAGE + S::OFF_PTS);
+          const int b = s * nsg + j0 + jj;
+          const int ni = min(io1 - io0, PCAP), nsm = min(so1 - so0, PCAP);
+          for (int e = lane; e < ni; e += 32) {
+            const int4 en = __ldg(P.inj + io0 + e);
+            const int rz = en.x / TX;
+            const float ccp = __ldg(cs + L.off(z0 + rz, 0, x0 + en.x % TX));
+            const float ser = __ldg(P.series + (long long)b * P.series_bstride + (long long)t * P.series_ld + en.y);
+            pts[32 + e] = en.x;
+            pts[32 + PCAP + e] = __float_as_int(ccp * (__int_as_float(en.z) * ser));
+          }
+          for (int e = lane; e < nsm; e += 32) {
+            const int2 en = __ldg(P.smp + so0 + e);
+            pts[32 + 2 * PCAP + e] = en.x;
+            pts[32 + 3 * PCAP + e] = en.y;
+          }
+          if (lane == 0) {
+            *reinterpret_cast<int4*>(pts) = make_int4(ni, nsm, io0, io1);
+            *reinterpret_cast<int2*>(pts + 4) = make_int2(so0, so1);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[st]);
+        }
+      }
+    }
+  }
+}
+
+// Warp 11, lane 0: items (n >= 1, k) in order; deps_ok = number of this CTA's
+// items whose 3 x 3 neighbourhood has finished the previous step (the items of
+// the first step need nothing and are counted from the start).
+__device__ __forceinline__ void watch_deps(const StepParams& P, int* deps_ok, int my_items,
+                                           volatile int* abort_flag) {
+  const int G = gridDim.x;
+  const int nic = my_items * P.nsteps;
+  for (int ic = my_items; ic < nic; ic++) {
+    const int n = ic / my_items, k = ic - n * my_items;
+    const int item = (int)blockIdx.x + k * G;
+    const int s = item / P.ntiles, tile = item - s * P.ntiles;
+    if (!wait_neighbours(P, s, tile, n, abort_flag)) return;
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(deps_ok)), "r"(ic + 1) : "memory");
+  }
+}
+
+// Warp 10, lane 0: progress flags.  Item ic of this CTA (step ic / my_items)
+// is complete when all consumer warps have counted it in wdone[ic % WDONE];
+// the flag (steps done) is then published with release semantics at GPU
+// scope.  Steps whose flags nobody reads (the launch's last) are skipped.
+__device__ __forceinline__ void publish(const StepParams& P, int* wdone, int my_items, volatile int* abort_flag) {
+  const int G = gridDim.x;
+  const int nic = my_items * (P.nsteps - 1);
+  for (int ic = 0; ic < nic; ic++) {
+    const int n = ic / my_items, k = ic - n * my_items;
+    const int target = NCW2D * (ic / WDONE + 1);
+    const long long t0 = clock64();
+    while (ld_acquire_cta_shared(&wdone[ic % WDONE]) < target) {
+      if (*abort_flag) return;
+      if (clock64() - t0 > WAIT_CYCLES) {
+        atomicCAS(P.status, 0, (int)FWI_ERR_TIMEOUT);
+        *abort_flag = 1;
+        return;
+      }
+      __nanosleep(64);
+    }
+    fence_acq_rel_gpu();
+    st_relaxed_gpu(P.done + (int)blockIdx.x + k * G, n + 1);
+  }
+}
+
+template <bool ADJ, int NS, bool ISO>
+__global__ void __launch_bounds__(NTHREADS2D, 1)
 step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_c, const Layout L, const Coef K, const StepParams P,
               int nitems) {
   using S = Smem2D<ADJ, NS>;
-  constexpr int NCW = TZ / R;  // warps
+  constexpr int R = R2D, NCW = NCW2D;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + S::nfloat * 4);
   uint64_t* empty = full + NS;
+  uint64_t* cfull = empty + NS;
+  uint64_t* cempty = cfull + 2;
+  int* wdone = reinterpret_cast<int*>(cempty + 2);
+  volatile int* abort_flag = wdone + WDONE;
+  int* deps_ok = wdone + WDONE + 1;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   const int my_items = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
   const int nsg = P.nsg;
-  const int n_it = my_items * nsg;
-  if (n_it == 0) return;
+  if (my_items == 0 || P.nsteps <= 0 || nsg <= 0) return;  // uniform over the CTA
 
   if (tid == 0) {
     tma_prefetch_desc(&tm_halo);
     tma_prefetch_desc(&tm_plain);
     tma_prefetch_desc(&tm_c);
     for (int i = 0; i < NS; i++) {
-      mbar_init(&full[i], 2);  // producer's expect_tx arrival + cp.async arrival
+      mbar_init(&full[i], 2);      // TMA expect_tx arrival + point-list arrival
       mbar_init(&empty[i], NCW);
     }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&cfull[i], 1);
+      mbar_init(&cempty[i], NCW);
+    }
+    for (int i = 0; i < WDONE; i++) wdone[i] = 0;
+    *abort_flag = 0;
+    *deps_ok = my_items;
     fence_mbar_init();
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- producer
-  constexpr uint32_t TX_BYTES = (S::IN + S::PV + (ADJ ? S::IN : 0)) * 4;
-  const bool producer = warp == NCW - 1 && lane == 0;
-  int pit = 0, pst = 0, pj = 0, ps = 0, ptile = blockIdx.x;
-  uint32_t pround = 0;  // parity of the ring round of the next load
-  while (ptile >= P.ntiles) { ptile -= P.ntiles; ps++; }
-  auto issue_next = [&]() {
-    const int b = ps * nsg + pj;
-    const int x0_ = (ptile % P.ntx) * TX, z0_ = (ptile / P.ntx) * TZ;
-    float* base = sm + pst * S::STAGE;
-    int* idx = reinterpret_cast<int*>(base + S::OFF_IDX);
-    const int* io = P.inj_off + b * P.inj_bstride + ptile;
-    const int* so = P.smp_off + b * P.smp_bstride + ptile;
-    cp_async4(idx + 0, io);
-    cp_async4(idx + 1, io + 1);
-    cp_async4(idx + 2, so);
-    cp_async4(idx + 3, so + 1);
-    cp_async_arrive(&full[pst]);
-    mbar_arrive_expect_tx(&full[pst], TX_BYTES + (pj == 0 ? S::PV * 4 : 0));
-    tma_load_4d(base, &tm_halo, x0_, z0_, b, P.s_cur, &full[pst]);
-    tma_load_4d(base + S::IN, &tm_plain, x0_ + HALO, z0_ + HALO, b, P.s_prev, &full[pst]);
-    if (ADJ) tma_load_4d(base + S::OFF_SNAP, &tm_halo, x0_, z0_, b, P.s_snap, &full[pst]);
-    if (pj == 0) tma_load_3d(base + S::OFF_C, &tm_c, x0_ + HALO, z0_ + HALO, ps, &full[pst]);
-    pit++;
-    if (++pst == NS) { pst = 0; pround ^= 1; }
-    if (++pj == nsg) {
-      pj = 0;
-      ptile += G;
-      while (ptile >= P.ntiles) { ptile -= P.ntiles; ps++; }
-    }
-  };
-  // Refill every stage whose previous occupant all warps have released; block
-  // only for the load of iteration `need` (the one this warp waits on next).
-  auto refill = [&](int need) -> bool {
-    while (pit < n_it && pit < need + NS) {
-      if (pit >= NS) {
-        if (pit <= need) {
-          if (!mbar_wait_bounded(&empty[pst], pround ^ 1, P.status)) return false;
-        } else if (!mbar_try_wait(&empty[pst], pround ^ 1)) {
-          break;
-        }
-      }
-      issue_next();
-    }
-    return true;
-  };
+  if (warp >= NCW) {  // ------------------------------------------- producer warpgroup
+    setmaxnreg_dec<REG_PRODUCER>();
+    if (warp == NCW && lane == 0)
+      produce_tma<ADJ, NS>(&tm_halo, &tm_plain, &tm_c, P, sm, full, empty, cfull, cempty, deps_ok, my_items,
+                           abort_flag);
+    else if (warp == NCW + 1)
+      produce_points<ADJ, NS>(L, P, sm, full, empty, my_items, lane, abort_flag);
+    else if (warp == NCW + 2 && lane == 0)
+      publish(P, wdone, my_items, abort_flag);
+    else if (warp == NCW + 3 && lane == 0)
+      watch_deps(P, deps_ok, my_items, abort_flag);
+    return;
+  }
+  setmaxnreg_inc<REG_CONSUMER>();
 
   // ------------------------------------------------------------------ consumers
   const int lx = 4 * lane, lz = R * warp;
@@ -193,7 +409,9 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   // next item's imaging accumulator rows (adjoint) and sponge table entries
   float4 gpre[R];
   float gzpre[R], gxpre[4];
-  auto prefetch_item = [&](int s_, int tile_) {
+  auto prefetch_item = [&](int k_) {
+    const int item_ = (int)blockIdx.x + k_ * G;
+    const int s_ = item_ / P.ntiles, tile_ = item_ - s_ * P.ntiles;
     const int gx_ = (tile_ % P.ntx) * TX + lx, zb = (tile_ / P.ntx) * TZ + lz;
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -206,138 +424,184 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
 #pragma unroll
     for (int q = 0; q < 4; q++) gxpre[q] = gx_ + q < L.nxp ? __ldg(gxt + gx_ + q) : 0.f;
   };
-  int s = 0, tile = blockIdx.x;
-  while (tile >= P.ntiles) { tile -= P.ntiles; s++; }
-  prefetch_item(s, tile);
+  // With one item per CTA the adjoint keeps the accumulator in registers
+  // across steps (a prefetch would read the rows before this thread stores them).
+  const bool carry = my_items == 1;
+  prefetch_item(0);
+  float gacc[R][4];
 
   int st = 0;
-  uint32_t round = 0;
-  int it = 0;
-  for (int k = 0; k < my_items; k++) {
-    // ---- new work item: sponge coefficients, output base, prefetch of the next item
-    const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
-    const int gx = x0 + lx;
-    const bool colv0 = gx < L.nxp, live = z0 + lz < L.nzp;
-    const bool sponge = L.nb > 0 && (x0 < L.nb || x0 + TX > L.nb + L.nx || z0 < L.nb || z0 + TZ > L.nb + L.nz);
-    bool rowv[R];
-    float cc[R][4], bc[R][4], gacc[R][4];
+  uint32_t ph = 0;
+  int ic = 0;
+  for (int n = 0; n < P.nsteps; n++) {
+    const int4 d = __ldg(reinterpret_cast<const int4*>(P.steps + n));
+    const int t = __ldg(&P.steps[n].t);
+    for (int k = 0; k < my_items; k++, ic++) {
+      const int item = (int)blockIdx.x + k * G;
+      const int s = item / P.ntiles, tile = item - s * P.ntiles;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      const int gx = x0 + lx;
+      const bool colv0 = gx < L.nxp, live = z0 + lz < L.nzp;
+      const bool sponge =
+          L.nb > 0 && (x0 < L.nb || x0 + TX > L.nb + L.nx || z0 < L.nb || z0 + TZ > L.nb + L.nz);
+      bool rowv[R];
+      float cc[R][4], bc[R][4];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-      rowv[r] = z0 + lz + r < L.nzp;
+      for (int r = 0; r < R; r++) {
+        rowv[r] = z0 + lz + r < L.nzp;
 #pragma unroll
-      for (int q = 0; q < 4; q++) bc[r][q] = sponge ? sponge_b(gzpre[r] + gxpre[q]) : 1.f;
-      if (ADJ) {
-        gacc[r][0] = gpre[r].x; gacc[r][1] = gpre[r].y; gacc[r][2] = gpre[r].z; gacc[r][3] = gpre[r].w;
-      }
-    }
-    const long long row0 = L.off(z0 + lz, 0, gx);
-    float* obase = P.pool + (long long)P.s_out * P.slot_elems + (long long)s * nsg * L.field + row0;
-    int ntile = tile + G, ns_ = s;
-    while (ntile >= P.ntiles) { ntile -= P.ntiles; ns_++; }
-    if (k + 1 < my_items) prefetch_item(ns_, ntile);
-
-    for (int j = 0; j < nsg; j++, it++) {
-      const int b = s * nsg + j;
-      if (producer && !refill(it)) return;
-      if (!mbar_wait_bounded(&full[st], round, P.status)) return;
-
-      float* I = sm + st * S::STAGE;
-      float* PV = I + S::IN;
-      const int4 off = *reinterpret_cast<const int4*>(I + S::OFF_IDX);
-      if (j == 0) {
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          const float4 c4 = lds4(I + S::OFF_C + (lz + r) * TX + lx);
-          cc[r][0] = c4.x; cc[r][1] = c4.y; cc[r][2] = c4.z; cc[r][3] = c4.w;
+        for (int q = 0; q < 4; q++) bc[r][q] = sponge ? sponge_b(gzpre[r] + gxpre[q]) : 1.f;
+        if (ADJ && (!carry || ic == 0)) {
+          gacc[r][0] = gpre[r].x; gacc[r][1] = gpre[r].y; gacc[r][2] = gpre[r].z; gacc[r][3] = gpre[r].w;
         }
       }
-      if (live) {
-        float lap[R][4], ctr[R][4], nv[R][4];
-        lap_block<R, ISO>(I, lz, lx, K, lap, ctr);
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-          const float4 pm = lds4(PV + (lz + r) * TX + lx);
-          const float pmv[4] = {pm.x, pm.y, pm.z, pm.w};
-#pragma unroll
-          for (int q = 0; q < 4; q++)
-            nv[r][q] = fmaf(cc[r][q], lap[r][q], fmaf(bc[r][q], ctr[r][q] - pmv[q], ctr[r][q]));
-        }
-        // Injection (sources in the forward, residual at receivers in the
-        // adjoint) and sampling (receivers in the forward, sources in the
-        // adjoint), staged in this warp's own rows of PV.
-        if (off.y > off.x || off.w > off.z) {
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < R; r++)
-            *reinterpret_cast<float4*>(PV + (lz + r) * TX + lx) = make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
-          __syncwarp();
-          for (int e = off.x + lane; e < off.y; e += 32) {
-            const int4 en = P.inj[e];
-            const int rz = en.x / TX;
-            if (rz < lz || rz >= lz + R) continue;
-            const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z0 + rz, 0, x0 + en.x % TX));
-            PV[en.x] += ccp * (__int_as_float(en.z) *
-                               P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
-          }
-          __syncwarp();
+      const long long row0 = L.off(z0 + lz, 0, gx);
+      float* obase = P.pool + (long long)d.z * P.slot_elems + (long long)s * nsg * L.field + row0;
+      if (!carry) prefetch_item(k + 1 < my_items ? k + 1 : 0);
+
+      for (int j = 0; j < nsg; j++) {
+        const int b = s * nsg + j;
+        if (!mbar_wait_abortable(&full[st], ph, P.status, abort_flag)) return;
+        float* I = sm + st * S::STAGE;
+        float* PV = I + S::IN;
+        const int* pts = reinterpret_cast<const int*>(I + S::OFF_PTS);
+        if (j == 0) {
+          const int cs = ic & 1;
+          if (!mbar_wait_abortable(&cfull[cs], (uint32_t)((ic >> 1) & 1), P.status, abort_flag)) return;
+          const float* C = sm + S::OFF_C + cs * S::PV;
 #pragma unroll
           for (int r = 0; r < R; r++) {
-            const float4 v = lds4(PV + (lz + r) * TX + lx);
-            nv[r][0] = v.x; nv[r][1] = v.y; nv[r][2] = v.z; nv[r][3] = v.w;
+            const float4 c4 = lds4(C + (lz + r) * TX + lx);
+            cc[r][0] = c4.x; cc[r][1] = c4.y; cc[r][2] = c4.z; cc[r][3] = c4.w;
           }
-          for (int e = off.z + lane; e < off.w; e += 32) {
-            const int2 en = P.smp[e];
-            const int rz = en.x / TX;
-            if (rz < lz || rz >= lz + R) continue;
-            P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = PV[en.x];
-          }
-          // generic-proxy writes to the stage are ordered before the TMA that refills it
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&cempty[cs]);
         }
-        if (ADJ) {
-          float lps[R][4], dummy[R][4];
-          lap_block<R, ISO>(I + S::OFF_SNAP, lz, lx, K, lps, dummy);
+        float nv[R][4];
+        if (live) {
+          float lap[R][4], ctr[R][4];
+          lap_block<R, ISO>(I, lz, lx, K, lap, ctr);
 #pragma unroll
-          for (int r = 0; r < R; r++)
+          for (int r = 0; r < R; r++) {
+            const float4 pm = lds4(PV + (lz + r) * TX + lx);
+            const float pmv[4] = {pm.x, pm.y, pm.z, pm.w};
 #pragma unroll
-            for (int q = 0; q < 4; q++) gacc[r][q] = fmaf(nv[r][q], lps[r][q], gacc[r][q]);
+            for (int q = 0; q < 4; q++)
+              nv[r][q] = fmaf(cc[r][q], lap[r][q], fmaf(bc[r][q], ctr[r][q] - pmv[q], ctr[r][q]));
+          }
+          const int4 h = *reinterpret_cast<const int4*>(pts);        // staged counts, injection range
+          const int2 h2 = *reinterpret_cast<const int2*>(pts + 4);   // sampling range
+          if (h.z < h.w || h2.x < h2.y) {
+            // Injection (sources in the forward, residual at receivers in the
+            // adjoint) and sampling (receivers in the forward, sources in the
+            // adjoint), staged in this warp's own rows of the consumed p^{n-1} tile.
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; r++)
+              *reinterpret_cast<float4*>(PV + (lz + r) * TX + lx) =
+                  make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
+            __syncwarp();
+            for (int e0 = 0; e0 < h.x; e0 += 32) {
+              const int e = e0 + lane;
+              int loc = -1 - lane;  // unique key for lanes without an entry of this warp
+              float val = 0.f;
+              if (e < h.x) {
+                const int l = pts[32 + e];
+                const int rz = l / TX;
+                if (rz >= lz && rz < lz + R) {
+                  loc = l;
+                  val = __int_as_float(pts[32 + PCAP + e]);
+                }
+              }
+              const unsigned peers = __match_any_sync(0xffffffffu, loc);
+              if (__any_sync(0xffffffffu, loc >= 0 && peers != (1u << lane))) {
+                // coincident points in this chunk: add them in entry order
+                for (int i = 0; i < 32; i++) {
+                  const int li = __shfl_sync(0xffffffffu, loc, i);
+                  const float vi = __shfl_sync(0xffffffffu, val, i);
+                  if (lane == 0 && li >= 0) PV[li] += vi;
+                }
+              } else if (loc >= 0) {
+                PV[loc] += val;
+              }
+              __syncwarp();
+            }
+            if (h.w - h.z > PCAP && lane == 0) {  // entries beyond the staged ones, in order
+              for (int e = h.z + PCAP; e < h.w; e++) {
+                const int4 en = P.inj[e];
+                const int rz = en.x / TX;
+                if (rz < lz || rz >= lz + R) continue;
+                const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z0 + rz, 0, x0 + en.x % TX));
+                const float ser =
+                    P.series[(long long)b * P.series_bstride + (long long)t * P.series_ld + en.y];
+                PV[en.x] += ccp * (__int_as_float(en.z) * ser);
+              }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+              const float4 v = lds4(PV + (lz + r) * TX + lx);
+              nv[r][0] = v.x; nv[r][1] = v.y; nv[r][2] = v.z; nv[r][3] = v.w;
+            }
+            float* so = P.smp_out + (long long)b * P.smp_bstride_out + (long long)t * P.smp_ld;
+            for (int e = lane; e < h.y; e += 32) {
+              const int l = pts[32 + 2 * PCAP + e];
+              const int rz = l / TX;
+              if (rz >= lz && rz < lz + R) so[pts[32 + 3 * PCAP + e]] = PV[l];
+            }
+            for (int e = h2.x + PCAP + lane; e < h2.y; e += 32) {
+              const int2 en = P.smp[e];
+              const int rz = en.x / TX;
+              if (rz >= lz && rz < lz + R) so[en.y] = PV[en.x];
+            }
+            // generic-proxy writes to the stage are ordered before the TMA that refills it
+            fence_proxy_async_shared();
+          }
+          if (ADJ) {
+            float lps[R][4], dummy[R][4];
+            lap_block<R, ISO>(I + S::OFF_SNAP, lz, lx, K, lps, dummy);
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+              for (int q = 0; q < 4; q++) gacc[r][q] = fmaf(nv[r][q], lps[r][q], gacc[r][q]);
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
-        float* o = obase + (long long)j * L.field;
+        if (live) {
+          float* o = obase + (long long)j * L.field;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            if (!rowv[r] || !colv0) continue;
+            if (gx + 3 < L.nxp) {
+              *reinterpret_cast<float4*>(o + r * L.SX) = make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; q++)
+                if (gx + q < L.nxp) o[r * L.SX + q] = nv[r][q];
+            }
+          }
+        }
+        if (++st == NS) { st = 0; ph ^= 1; }
+      }
+      if (ADJ && live) {
+        float* gb = P.grad + (long long)s * L.field + row0;
 #pragma unroll
         for (int r = 0; r < R; r++) {
           if (!rowv[r] || !colv0) continue;
           if (gx + 3 < L.nxp) {
-            *reinterpret_cast<float4*>(o + r * L.SX) = make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
+            *reinterpret_cast<float4*>(gb + r * L.SX) = make_float4(gacc[r][0], gacc[r][1], gacc[r][2], gacc[r][3]);
           } else {
 #pragma unroll
             for (int q = 0; q < 4; q++)
-              if (gx + q < L.nxp) o[r * L.SX + q] = nv[r][q];
+              if (gx + q < L.nxp) gb[r * L.SX + q] = gacc[r][q];
           }
         }
-      } else {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
       }
-      if (++st == NS) { st = 0; round ^= 1; }
+      // this warp's stores of the item are done: count it for the publisher
+      __syncwarp();
+      if (lane == 0) red_release_cta_shared(&wdone[ic % WDONE], 1);
     }
-    if (ADJ && live) {
-      float* o = P.grad + (long long)s * L.field + row0;
-#pragma unroll
-      for (int r = 0; r < R; r++) {
-        if (!rowv[r] || !colv0) continue;
-        if (gx + 3 < L.nxp) {
-          *reinterpret_cast<float4*>(o + r * L.SX) = make_float4(gacc[r][0], gacc[r][1], gacc[r][2], gacc[r][3]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; q++)
-            if (gx + q < L.nxp) o[r * L.SX + q] = gacc[r][q];
-        }
-      }
-    }
-    s = ns_;
-    tile = ntile;
   }
 }
 
@@ -352,33 +616,42 @@ static int num_sms() {
   return n;
 }
 
-// Compiled variants (R rows per thread, i.e. 32*32/R threads; ring depth NS).  The
-// arithmetic per grid point is the same in every variant, so their results
-// are bit-identical; the autotuner in fwi_api.cu picks the fastest per call shape.
-template <bool ADJ, int NS, int R, bool ISO>
+// Compiled variants differ in the ring depth NS only; the arithmetic per grid
+// point is the same in every variant, so their results are bit-identical and
+// the autotuner in fwi_api.cu picks the fastest per call shape.  The launch is
+// cooperative: CTAs wait on one another's progress flags, so all of them must
+// be resident (one per SM).
+template <bool ADJ, int NS, bool ISO>
 static cudaError_t launch_iso(const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc, const Layout& L,
                               const Coef& K, const StepParams& P, int nsamp, cudaStream_t st) {
   using S = Smem2D<ADJ, NS>;
-  constexpr int NT = 32 * (TZ / R);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ADJ, NS, R, ISO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ADJ, NS, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         S::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int nitems = P.ntiles * nsamp;
-  const int grid = nitems < num_sms() ? nitems : num_sms();
-  step2d_kernel<ADJ, NS, R, ISO><<<grid, NT, S::bytes, st>>>(th, tp, tc, L, K, P, nitems);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nitems < num_sms() ? nitems : num_sms());
+  cfg.blockDim = dim3(NTHREADS2D);
+  cfg.dynamicSmemBytes = S::bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, step2d_kernel<ADJ, NS, ISO>, th, tp, tc, L, K, P, nitems);
 }
 
-template <bool ADJ, int NS, int R>
+template <bool ADJ, int NS>
 static cudaError_t launch_variant(const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
                                   const Layout& L, const Coef& K, const StepParams& P, int nsamp, cudaStream_t st) {
   if (K.cx[1] == K.cz[1] && K.cx[2] == K.cz[2] && K.cx[3] == K.cz[3] && K.cx[4] == K.cz[4])
-    return launch_iso<ADJ, NS, R, true>(th, tp, tc, L, K, P, nsamp, st);
-  return launch_iso<ADJ, NS, R, false>(th, tp, tc, L, K, P, nsamp, st);
+    return launch_iso<ADJ, NS, true>(th, tp, tc, L, K, P, nsamp, st);
+  return launch_iso<ADJ, NS, false>(th, tp, tc, L, K, P, nsamp, st);
 }
 
 struct Variant2D {
@@ -388,19 +661,17 @@ struct Variant2D {
 };
 
 static const Variant2D kFwd2D[] = {
-    {"fwd2d R4 NS4 (8 warps)", launch_variant<false, 4, 4>},
-    {"fwd2d R4 NS3 (8 warps)", launch_variant<false, 3, 4>},
-    {"fwd2d R2 NS4 (16 warps)", launch_variant<false, 4, 2>},
-    {"fwd2d R2 NS3 (16 warps)", launch_variant<false, 3, 2>},
+    {"fwd2d NS4 (8+4 warps)", launch_variant<false, 4>},
+    {"fwd2d NS3 (8+4 warps)", launch_variant<false, 3>},
 };
 static const Variant2D kAdj2D[] = {
-    {"adj2d R4 NS3 (8 warps)", launch_variant<true, 3, 4>},
-    {"adj2d R4 NS2 (8 warps)", launch_variant<true, 2, 4>},
-    {"adj2d R2 NS3 (16 warps)", launch_variant<true, 3, 2>},
-    {"adj2d R2 NS2 (16 warps)", launch_variant<true, 2, 2>},
+    {"adj2d NS3 (8+4 warps)", launch_variant<true, 3>},
+    {"adj2d NS2 (8+4 warps)", launch_variant<true, 2>},
 };
 
-int num_variants2d(bool adj) { return adj ? (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0])) : (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0])); }
+int num_variants2d(bool adj) {
+  return adj ? (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0])) : (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0]));
+}
 
 const char* variant2d_name(bool adj, int v) {
   if (v < 0 || v >= num_variants2d(adj)) return "invalid";
