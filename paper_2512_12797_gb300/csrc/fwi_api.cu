@@ -528,13 +528,23 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
 // and keep the fastest.  Runs once per wavefield count; synchronises the
 // stream while it times.
 int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
-             cudaStream_t st) {
+             long long nslots, cudaStream_t st) {
   const int B = nsamp * nsg;
   if (C->L.ndim == 3) {
     C->var[0] = C->var[1] = 0;
     return FWI_OK;
   }
   if (C->tuned_B == B && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
+  // timing steps with the traffic of real ones: the three ring slots rotate
+  // (whatever they hold), the snapshot comes from a fourth slot when there is one
+  {
+    StepDesc td[kTuneSteps];
+    for (int i = 0; i < kTuneSteps; i++)
+      td[i] = make_desc(Plan::RING + i % 3, Plan::RING + (i + 2) % 3, Plan::RING + (i + 1) % 3,
+                        nslots > Plan::QR ? Plan::QR : Plan::ZERO, 0);
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(C->tdesc, td, sizeof(td), cudaMemcpyHostToDevice));
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -549,7 +559,7 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtens
     P.inj_bstride = 0;
     P.inj = C->rec_inj;
     P.series = C->wav;
-    P.steps = C->tdesc;  // zero slot in, one ring slot out, every step
+    P.steps = C->tdesc;
     P.nsteps = kTuneSteps;
     P.done = C->done;
     const size_t done_bytes = (size_t)nsamp * C->ntiles * 4;
@@ -765,14 +775,7 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
-  {
-    std::vector<StepDesc> td(kTuneSteps);
-    for (int i = 0; i < kTuneSteps; i++) td[i] = StepDesc{Plan::ZERO, Plan::ZERO, Plan::RING, Plan::ZERO, 0, {0, 0, 0}};
-    if (cudaMemcpy(C->tdesc, td.data(), td.size() * sizeof(StepDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
-      fwi_destroy(C);
-      return FWI_ERR_CUDA;
-    }
-  }
+
   for (int i = 0; i < 5; i++)
     if (cudaEventCreate(&C->ev[i]) != cudaSuccess) {
       fwi_destroy(C);
@@ -879,7 +882,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   if (nslots < 4) return FWI_ERR_OOM;
   CUtensorMap th, tp, tc, tg;
   if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, st)) != FWI_OK) return rc;
+  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
@@ -915,7 +918,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   C->slots_avail = nslots;
   CUtensorMap th, tp, tc, tg;
   if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, st)) != FWI_OK) return rc;
+  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;

@@ -48,7 +48,7 @@ namespace fwi {
 constexpr int R2D = 4;                       // rows per consumer thread
 constexpr int NCW2D = TZ / R2D;              // consumer warps (8)
 constexpr int NTHREADS2D = 32 * NCW2D + 128;  // + producer warpgroup
-constexpr int PCAP = 256;                    // point-list entries staged per stage and list
+constexpr int PCAP = 128;                    // point-list entries staged per stage and list
 constexpr int WDONE = 8;                     // item-completion counters (ring)
 constexpr int REG_LAUNCH = 168, REG_PRODUCER = 72, REG_CONSUMER = 216;
 static_assert(128 * REG_PRODUCER + 32 * NCW2D * REG_CONSUMER <= NTHREADS2D * REG_LAUNCH,
@@ -272,25 +272,47 @@ __device__ __forceinline__ void produce_points(const Layout& L, const StepParams
           const int io0 = __shfl_sync(0xffffffffu, a0, jj), io1 = __shfl_sync(0xffffffffu, a1, jj);
           const int so0 = __shfl_sync(0xffffffffu, b0, jj), so1 = __shfl_sync(0xffffffffu, b1, jj);
           const int st = m % NS;
+          const int b = s * nsg + j0 + jj;
+          const int ni = min(io1 - io0, PCAP), nsm = min(so1 - so0, PCAP);
+          // all loads before the wait for the stage, so that their latency
+          // overlaps the consumers' work on it
+          constexpr int NCH = PCAP / 32;
+          int4 ie[NCH];
+          int2 se[NCH];
+#pragma unroll
+          for (int c = 0; c < NCH; c++) {
+            const int e = c * 32 + lane;
+            ie[c] = e < ni ? __ldg(P.inj + io0 + e) : make_int4(0, 0, 0, 0);
+            se[c] = e < nsm ? __ldg(P.smp + so0 + e) : make_int2(0, 0);
+          }
+          float iv[NCH];
+#pragma unroll
+          for (int c = 0; c < NCH; c++) {
+            iv[c] = 0.f;
+            if (c * 32 + lane < ni) {
+              const int rz = ie[c].x / TX;
+              const float ccp = __ldg(cs + L.off(z0 + rz, 0, x0 + ie[c].x % TX));
+              const float ser =
+                  __ldg(P.series + (long long)b * P.series_bstride + (long long)t * P.series_ld + ie[c].y);
+              iv[c] = ccp * (__int_as_float(ie[c].z) * ser);
+            }
+          }
           int ok = 1;
           if (m >= NS && lane == 0)
             ok = mbar_wait_abortable(&empty[st], (uint32_t)((m / NS - 1) & 1), P.status, abort_flag);
           if (!__shfl_sync(0xffffffffu, ok, 0)) return;
           int* pts = reinterpret_cast<int*>(sm + st * S::STAGE + S::OFF_PTS);
-          const int b = s * nsg + j0 + jj;
-          const int ni = min(io1 - io0, PCAP), nsm = min(so1 - so0, PCAP);
-          for (int e = lane; e < ni; e += 32) {
-            const int4 en = __ldg(P.inj + io0 + e);
-            const int rz = en.x / TX;
-            const float ccp = __ldg(cs + L.off(z0 + rz, 0, x0 + en.x % TX));
-            const float ser = __ldg(P.series + (long long)b * P.series_bstride + (long long)t * P.series_ld + en.y);
-            pts[32 + e] = en.x;
-            pts[32 + PCAP + e] = __float_as_int(ccp * (__int_as_float(en.z) * ser));
-          }
-          for (int e = lane; e < nsm; e += 32) {
-            const int2 en = __ldg(P.smp + so0 + e);
-            pts[32 + 2 * PCAP + e] = en.x;
-            pts[32 + 3 * PCAP + e] = en.y;
+#pragma unroll
+          for (int c = 0; c < NCH; c++) {
+            const int e = c * 32 + lane;
+            if (e < ni) {
+              pts[32 + e] = ie[c].x;
+              pts[32 + PCAP + e] = __float_as_int(iv[c]);
+            }
+            if (e < nsm) {
+              pts[32 + 2 * PCAP + e] = se[c].x;
+              pts[32 + 3 * PCAP + e] = se[c].y;
+            }
           }
           if (lane == 0) {
             *reinterpret_cast<int4*>(pts) = make_int4(ni, nsm, io0, io1);
