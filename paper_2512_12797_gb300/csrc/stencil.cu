@@ -53,7 +53,12 @@ constexpr int WDONE = 8;                     // item-completion counters (ring)
 constexpr int REG_LAUNCH = 168, REG_PRODUCER = 72, REG_CONSUMER = 216;
 static_assert(128 * REG_PRODUCER + 32 * NCW2D * REG_CONSUMER <= NTHREADS2D * REG_LAUNCH,
               "register split exceeds the launch allocation");
-
+// L2 eviction priorities: the cc tiles and the imaging accumulator, re-read
+// every step, are kept (evict-last); the older level and the output, which
+// stream through once per step, go first; the halo tiles of the stepped level
+// and of the snapshot keep the normal priority so that neighbouring tiles
+// find their overlap in L2.
+constexpr bool kL2Hints = true;
 // One ring stage: halo tile of the stepped level, plain tile of the older
 // level, [halo tile of the snapshot], and the iteration's point lists:
 //   PTS[0..5]   = staged injection count, staged sampling count, global
@@ -82,7 +87,12 @@ __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cas
 // shared row r0+4, column c0+4 of a halo tile T (row stride HX).  With
 // ISO (hx == hz) the two axes share coefficients and each k costs one bracket
 // [(x_{+k} + x_{-k}) + (z_{+k} + z_{-k}) - 4p], also exactly zero for a
-// constant field.
+// constant field.  Adjacent columns are computed as pairs with the packed
+// FP32 instructions (two independent IEEE operations each, so every point
+// sees exactly the operations of the scalar form); x - y is formed as
+// fma(y, -1, x) and x - 4p as fma(-4, p, x), both exact rewrites.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 template <int R, bool ISO>
 __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, int c0, const Coef& K,
                                           float (&lap)[R][4], float (&ctr)[R][4]) {
@@ -90,6 +100,7 @@ __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, i
 #pragma unroll
   for (int i = 0; i < R + 8; i++) zc[i] = lds4(T + (r0 + i) * HX + c0 + 4);
   const float* zp = reinterpret_cast<const float*>(&zc[0]);  // zc[i] component j is zp[4*i + j]
+  const float2 m1 = f2(-1.f, -1.f), m4 = f2(-4.f, -4.f);
 #pragma unroll
   for (int r = 0; r < R; r++) {
     const float4 xl = lds4(T + (r0 + r + 4) * HX + c0);
@@ -97,28 +108,36 @@ __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, i
     const float4 ce = zc[r + 4];
     const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const float p = w[4 + j];
+    for (int j = 0; j < 4; j += 2) {
+      const float2 p = f2(w[4 + j], w[5 + j]);
+      // (x_{+k} + x_{-k}) and (z_{+k} + z_{-k}) of the pair
+      auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+      auto zs = [&](int k) {
+        return __fadd2_rn(f2(zp[4 * (r + 4 + k) + j], zp[4 * (r + 4 + k) + j + 1]),
+                          f2(zp[4 * (r + 4 - k) + j], zp[4 * (r + 4 - k) + j + 1]));
+      };
+      float2 a;
       if (ISO) {
-        const float p4 = 4.f * p;
-        float a = K.cx[4] * (((w[8 + j] + w[j]) + (zp[4 * (r + 8) + j] + zp[4 * r + j])) - p4);
-        a = fmaf(K.cx[3], ((w[7 + j] + w[1 + j]) + (zp[4 * (r + 7) + j] + zp[4 * (r + 1) + j])) - p4, a);
-        a = fmaf(K.cx[2], ((w[6 + j] + w[2 + j]) + (zp[4 * (r + 6) + j] + zp[4 * (r + 2) + j])) - p4, a);
-        a = fmaf(K.cx[1], ((w[5 + j] + w[3 + j]) + (zp[4 * (r + 5) + j] + zp[4 * (r + 3) + j])) - p4, a);
-        lap[r][j] = a;
+        auto br = [&](int k) { return __ffma2_rn(m4, p, __fadd2_rn(xs(k), zs(k))); };
+        a = __fmul2_rn(f2(K.cx[4], K.cx[4]), br(4));
+        a = __ffma2_rn(f2(K.cx[3], K.cx[3]), br(3), a);
+        a = __ffma2_rn(f2(K.cx[2], K.cx[2]), br(2), a);
+        a = __ffma2_rn(f2(K.cx[1], K.cx[1]), br(1), a);
       } else {
-        const float p2 = p + p;
-        float sx = K.cx[4] * ((w[8 + j] + w[j]) - p2);
-        sx = fmaf(K.cx[3], (w[7 + j] + w[1 + j]) - p2, sx);
-        sx = fmaf(K.cx[2], (w[6 + j] + w[2 + j]) - p2, sx);
-        sx = fmaf(K.cx[1], (w[5 + j] + w[3 + j]) - p2, sx);
-        float sz = fmaf(K.cz[4], (zp[4 * (r + 8) + j] + zp[4 * r + j]) - p2, sx);
-        sz = fmaf(K.cz[3], (zp[4 * (r + 7) + j] + zp[4 * (r + 1) + j]) - p2, sz);
-        sz = fmaf(K.cz[2], (zp[4 * (r + 6) + j] + zp[4 * (r + 2) + j]) - p2, sz);
-        sz = fmaf(K.cz[1], (zp[4 * (r + 5) + j] + zp[4 * (r + 3) + j]) - p2, sz);
-        lap[r][j] = sz;
+        const float2 p2 = __fadd2_rn(p, p);
+        a = __fmul2_rn(f2(K.cx[4], K.cx[4]), __ffma2_rn(p2, m1, xs(4)));
+        a = __ffma2_rn(f2(K.cx[3], K.cx[3]), __ffma2_rn(p2, m1, xs(3)), a);
+        a = __ffma2_rn(f2(K.cx[2], K.cx[2]), __ffma2_rn(p2, m1, xs(2)), a);
+        a = __ffma2_rn(f2(K.cx[1], K.cx[1]), __ffma2_rn(p2, m1, xs(1)), a);
+        a = __ffma2_rn(f2(K.cz[4], K.cz[4]), __ffma2_rn(p2, m1, zs(4)), a);
+        a = __ffma2_rn(f2(K.cz[3], K.cz[3]), __ffma2_rn(p2, m1, zs(3)), a);
+        a = __ffma2_rn(f2(K.cz[2], K.cz[2]), __ffma2_rn(p2, m1, zs(2)), a);
+        a = __ffma2_rn(f2(K.cz[1], K.cz[1]), __ffma2_rn(p2, m1, zs(1)), a);
       }
-      ctr[r][j] = p;
+      lap[r][j] = a.x;
+      lap[r][j + 1] = a.y;
+      ctr[r][j] = p.x;
+      ctr[r][j + 1] = p.y;
     }
   }
 }
@@ -175,6 +194,7 @@ __device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CU
   using S = Smem2D<ADJ, NS>;
   constexpr uint32_t TX_BYTES = (S::IN + S::PV + (ADJ ? S::IN : 0)) * 4;
   const int G = gridDim.x, nsg = P.nsg;
+  const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
   int m = 0, ic = 0;
   for (int n = 0; n < P.nsteps; n++) {
     const int4 d = __ldg(reinterpret_cast<const int4*>(P.steps + n));  // cur, prev, out, snap
@@ -200,7 +220,10 @@ __device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CU
         if (ic >= 2 && !mbar_wait_abortable(&cempty[cs], (uint32_t)(((ic >> 1) - 1) & 1), P.status, abort_flag))
           goto aborted;
         mbar_arrive_expect_tx(&cfull[cs], S::PV * 4);
-        tma_load_3d(sm + S::OFF_C + cs * S::PV, tm_c, x0 + HALO, z0 + HALO, s, &cfull[cs]);
+        if (kL2Hints)
+          tma_load_3d_hint(sm + S::OFF_C + cs * S::PV, tm_c, x0 + HALO, z0 + HALO, s, &cfull[cs], pol_last);
+        else
+          tma_load_3d(sm + S::OFF_C + cs * S::PV, tm_c, x0 + HALO, z0 + HALO, s, &cfull[cs]);
       }
       for (int j = 0; j < nsg; j++, m++) {
         const int st = m % NS;
@@ -210,7 +233,10 @@ __device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CU
         float* base = sm + st * S::STAGE;
         mbar_arrive_expect_tx(&full[st], TX_BYTES);
         tma_load_4d(base, tm_halo, x0, z0, b, d.x, &full[st]);
-        tma_load_4d(base + S::IN, tm_plain, x0 + HALO, z0 + HALO, b, d.y, &full[st]);
+        if (kL2Hints)
+          tma_load_4d_hint(base + S::IN, tm_plain, x0 + HALO, z0 + HALO, b, d.y, &full[st], pol_first);
+        else
+          tma_load_4d(base + S::IN, tm_plain, x0 + HALO, z0 + HALO, b, d.y, &full[st]);
         if (ADJ) tma_load_4d(base + S::OFF_SNAP, tm_halo, x0, z0, b, d.w, &full[st]);
       }
     }
@@ -426,6 +452,7 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
 
   // ------------------------------------------------------------------ consumers
   const int lx = 4 * lane, lz = R * warp;
+  const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
   const float* gzt = P.gtab;
   const float* gxt = P.gtab + L.nzp + L.nyp;
   // next item's imaging accumulator rows (adjoint) and sponge table entries
@@ -439,9 +466,11 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     for (int r = 0; r < R; r++) {
       const bool v = zb + r < L.nzp && gx_ < L.nxp;
       gzpre[r] = zb + r < L.nzp ? __ldg(gzt + zb + r) : 0.f;
-      if (ADJ)
-        gpre[r] = v ? *reinterpret_cast<const float4*>(P.grad + (long long)s_ * L.field + L.off(zb + r, 0, gx_))
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ADJ) {
+        const float* gp = P.grad + (long long)s_ * L.field + L.off(zb + r, 0, gx_);
+        gpre[r] = !v ? make_float4(0.f, 0.f, 0.f, 0.f)
+                     : (kL2Hints ? ld4_hint(gp, pol_last) : *reinterpret_cast<const float4*>(gp));
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; q++) gxpre[q] = gx_ + q < L.nxp ? __ldg(gxt + gx_ + q) : 0.f;
@@ -508,8 +537,14 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
             const float4 pm = lds4(PV + (lz + r) * TX + lx);
             const float pmv[4] = {pm.x, pm.y, pm.z, pm.w};
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-              nv[r][q] = fmaf(cc[r][q], lap[r][q], fmaf(bc[r][q], ctr[r][q] - pmv[q], ctr[r][q]));
+            for (int q = 0; q < 4; q += 2) {  // cc * lap + (ctr + bc * (ctr - pm)), in pairs
+              const float2 c2 = f2(ctr[r][q], ctr[r][q + 1]);
+              const float2 d2 = __ffma2_rn(f2(pmv[q], pmv[q + 1]), f2(-1.f, -1.f), c2);
+              const float2 n2 = __ffma2_rn(f2(cc[r][q], cc[r][q + 1]), f2(lap[r][q], lap[r][q + 1]),
+                                           __ffma2_rn(f2(bc[r][q], bc[r][q + 1]), d2, c2));
+              nv[r][q] = n2.x;
+              nv[r][q + 1] = n2.y;
+            }
           }
           const int4 h = *reinterpret_cast<const int4*>(pts);        // staged counts, injection range
           const int2 h2 = *reinterpret_cast<const int2*>(pts + 4);   // sampling range
@@ -585,7 +620,12 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
 #pragma unroll
             for (int r = 0; r < R; r++)
 #pragma unroll
-              for (int q = 0; q < 4; q++) gacc[r][q] = fmaf(nv[r][q], lps[r][q], gacc[r][q]);
+              for (int q = 0; q < 4; q += 2) {
+                const float2 g2 = __ffma2_rn(f2(nv[r][q], nv[r][q + 1]), f2(lps[r][q], lps[r][q + 1]),
+                                             f2(gacc[r][q], gacc[r][q + 1]));
+                gacc[r][q] = g2.x;
+                gacc[r][q + 1] = g2.y;
+              }
           }
         }
         __syncwarp();
@@ -596,7 +636,11 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
           for (int r = 0; r < R; r++) {
             if (!rowv[r] || !colv0) continue;
             if (gx + 3 < L.nxp) {
-              *reinterpret_cast<float4*>(o + r * L.SX) = make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
+              const float4 v4 = make_float4(nv[r][0], nv[r][1], nv[r][2], nv[r][3]);
+              if (kL2Hints)
+                st4_hint(o + r * L.SX, v4, pol_first);
+              else
+                *reinterpret_cast<float4*>(o + r * L.SX) = v4;
             } else {
 #pragma unroll
               for (int q = 0; q < 4; q++)
@@ -612,7 +656,11 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
         for (int r = 0; r < R; r++) {
           if (!rowv[r] || !colv0) continue;
           if (gx + 3 < L.nxp) {
-            *reinterpret_cast<float4*>(gb + r * L.SX) = make_float4(gacc[r][0], gacc[r][1], gacc[r][2], gacc[r][3]);
+            const float4 v4 = make_float4(gacc[r][0], gacc[r][1], gacc[r][2], gacc[r][3]);
+            if (kL2Hints)
+              st4_hint(gb + r * L.SX, v4, pol_last);
+            else
+              *reinterpret_cast<float4*>(gb + r * L.SX) = v4;
           } else {
 #pragma unroll
             for (int q = 0; q < 4; q++)
