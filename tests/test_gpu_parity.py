@@ -206,6 +206,15 @@ def test_velocity_above_stability_bound_sets_status(P, torch):
     perm, wt = P.encode(0, 0, w.ns)
     ctx.forward(v, perm, wt, [w.ns])
     assert ctx.device_status() == -2
+    # The error word also stops the multi-step launch: its warps see it at
+    # their next dependency wait, give up and drain their copies.  The
+    # context stays usable, and the next call is bit-identical to a fresh
+    # context's.
+    v[0, 5, 5] = 2000.0
+    d1 = ctx.forward(v, perm, wt, [w.ns])
+    assert ctx.device_status() == 0
+    d2 = make_ctx(P, w, 1).forward(v, perm, wt, [w.ns])
+    assert torch.equal(d1, d2)
 
 
 def test_all_step_kernel_variants_bit_identical(P, torch):
