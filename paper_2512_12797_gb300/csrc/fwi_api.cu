@@ -1025,8 +1025,16 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
   }
   // Samples per chunk: the whole batch when its checkpoint plan fits the pool,
   // otherwise the chunk size that minimises (chunks) x (2 nt + recomputed
-  // steps) x (time of one step launch), a launch costing at least ~8 us.
+  // steps) x (time of one step).  In 2D all steps of a phase share one launch
+  // and a step costs the work of the busiest CTA, ceil(items / SMs) tiles x
+  // nsg supergathers (~1.7 us per tile), but at least ~15 us: with about one
+  // item per CTA each step waits for its neighbours' previous one (flag,
+  // fence, poll, TMA latency); plus ~20 us per launch (three per checkpoint
+  // segment).  In 3D every step is a launch of at least ~8 us.
   const double pts = (double)C->L.nzp * C->L.nyp * C->L.nxp;
+  int nsm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
   int best_c = -1;
   double best_cost = 0.0;
   for (int c = nsamp; c >= 1; c--) {
@@ -1034,8 +1042,15 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
     Plan p;
     if (!make_plan(nt, (long long)(C->pool_bytes / slot_bytes), &p)) continue;
     const int nchunks = (nsamp + c - 1) / c;
-    const double t_launch = std::max(8e-6, c * nsg * pts * 16.0 / 6e12);
-    const double cost = nchunks * (2.0 * nt + (double)p.recompute) * t_launch;
+    double cost;
+    if (C->L.ndim == 2) {
+      const double per_cta = std::ceil((double)c * C->ntiles / nsm) * nsg;
+      cost = nchunks * ((2.0 * nt + (double)p.recompute) * std::max(per_cta * 1.7e-6, 15e-6) +
+                        (1.0 + 2.0 * (p.jL + 1)) * 20e-6);
+    } else {
+      const double t_launch = std::max(8e-6, c * nsg * pts * 16.0 / 6e12);
+      cost = nchunks * (2.0 * nt + (double)p.recompute) * t_launch;
+    }
     if (best_c < 0 || cost < best_cost * 0.999) {
       best_c = c;
       best_cost = cost;
