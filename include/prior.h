@@ -1,0 +1,51 @@
+// prior.h -- C ABI of the tensor-core kernels of the learned prior: the
+// network g_theta that predicts the clean model from a noisy one (Sec. 2.2,
+// eq. for x0-hat; trained on velocity-model patches, Sec. 3.1).  The network
+// is a small U-Net of 3x3 convolutions; these entry points run its
+// contractions in BF16 with FP32 accumulation on the tensor cores.
+//
+// Conventions: all pointers are device pointers owned by the caller and
+// 16-byte aligned; calls are asynchronous on `stream` (a cudaStream_t, null =
+// legacy default stream).  A return value < 0 is an argument or launch error
+// and nothing was launched, except PRIOR_ERR_CUDA, which carries a failed
+// launch.  Device-side timeouts of the kernels' bounded waits are recorded in
+// *status (a device int the caller zeroes; null selects an internal word read
+// by prior_last_status).
+#pragma once
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum prior_status {
+  PRIOR_OK = 0,
+  PRIOR_ERR_ARG = -1,
+  PRIOR_ERR_CUDA = -4,
+  PRIOR_ERR_TIMEOUT = -6,
+};
+
+// D = A * B^T (+ bias) (ReLU if relu != 0).
+//   A: [M][K] BF16 row-major (K contiguous); B: [N][K] BF16 row-major;
+//   D: [M][ldd] FP32 (d_bf16 = 0) or BF16 (d_bf16 = 1); bias: [N] FP32 or null.
+// Requires M % 128 == 0, K % 64 == 0 and N in {32, 64, 128, 256} or
+// N % 128 == 0; ldd >= N and ldd % 8 == 0.
+int prior_gemm_bf16(const void* A, const void* B, void* D, int M, int N, int K, int ldd, int d_bf16,
+                    const float* bias, int relu, int* status, void* stream);
+
+// Y = conv3x3(X, Wt) (+ bias) (ReLU if relu != 0), stride 1, zero padding 1
+// ("same" size), cross-correlation as in the usual CNN definition:
+//   Y[n][y][x][o] = sum_{dy,dx in 0..2} sum_c Wt[o][dy*3+dx][c] * X[n][y+dy-1][x+dx-1][c].
+//   X: [nimg][H][W][Cin] BF16 (NHWC); Wt: [Cout][9][Cin] BF16;
+//   Y: [nimg][H][W][Cout] FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1); bias: [Cout] FP32 or null.
+// Requires Cin % 64 == 0; Cout in {32, 64, 128, 256} or Cout % 128 == 0;
+// W a power of two <= 128 or a multiple of 128; H * min(W, 128) a multiple of 128.
+int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, int W, int Cin, int Cout,
+                       int y_bf16, const float* bias, int relu, int* status, void* stream);
+
+// Reads and clears the internal status word (synchronises the stream).
+int prior_last_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif

@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/fwi.h (argument marshalling only).
+"""ctypes declarations of the C ABI in include/fwi.h and include/prior.h
+(argument marshalling only).
 
 Loading fails loudly when libfwi.so is missing: there is no CPU fallback.
 """
@@ -16,6 +17,8 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradie
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
            "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error",
            "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking"]
+# every symbol prior.h declares
+PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_last_status"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -72,6 +75,11 @@ _SIGS = {
     "fwi_residual_misfit_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    _I32P, _I8P, _I32P, ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double, _P, _P, _P]),
+    "prior_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "prior_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "prior_last_status": (ctypes.c_int, [_P]),
 }
 
 

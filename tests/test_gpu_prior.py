@@ -1,0 +1,79 @@
+"""Parity of the learned prior's tensor-core kernels (tcgen05 BF16 GEMM and
+3x3 convolution, include/prior.h) with the FP64 oracle on the same BF16
+inputs.  Products of BF16 values are exact in FP32, so the only error is FP32
+accumulation: relative L2 error ~ sqrt(K) * 2^-24, bounded here by 2e-5."""
+import numpy as np
+import pytest
+
+from oracle import prior_oracle as PO
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2512_12797_gb300 import build
+    build.build()
+    from paper_2512_12797_gb300 import prior
+    return prior
+
+
+def _bf16(torch, shape, seed):
+    g = torch.Generator().manual_seed(seed)
+    return torch.randn(shape, generator=g).to(torch.bfloat16)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 32, 64), (256, 64, 192), (384, 128, 1024), (256, 256, 512),
+                                   (512, 384, 320)])
+def test_gemm_matches_oracle(P, M, N, K):
+    import torch
+    A, B = _bf16(torch, (M, K), 1 + M), _bf16(torch, (N, K), 2 + N)
+    D = P.gemm_bf16(A.cuda(), B.cuda())
+    ref = PO.gemm(A.float().numpy(), B.float().numpy())
+    assert _rel(D.cpu().double().numpy(), ref) < TOL
+    assert P.last_status() == 0
+
+
+def test_gemm_bias_relu_and_bf16_output(P):
+    import torch
+    M, N, K = 256, 64, 128
+    A, B = _bf16(torch, (M, K), 5), _bf16(torch, (N, K), 6)
+    bias = torch.linspace(-3, 3, N)
+    D = P.gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), relu=True, out_bf16=True)
+    ref = np.maximum(PO.gemm(A.float().numpy(), B.float().numpy()) + bias.double().numpy(), 0.0)
+    # one BF16 rounding of the output (relative 2^-9)
+    assert np.allclose(D.float().cpu().numpy(), ref, rtol=2 ** -8, atol=1e-3)
+    assert (D.float() >= 0).all()
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", [(2, 16, 16, 64, 32), (1, 32, 64, 128, 64), (1, 8, 128, 64, 128),
+                                            (1, 4, 256, 64, 256)])
+def test_conv3x3_matches_oracle(P, n, H, W, Cin, Cout):
+    import torch
+    X, Wt = _bf16(torch, (n, H, W, Cin), 7 + H), _bf16(torch, (Cout, 9, Cin), 8 + Cout)
+    bias = torch.randn(Cout, generator=torch.Generator().manual_seed(9))
+    Y = P.conv3x3(X.cuda(), Wt.cuda(), bias=bias.cuda(), out_bf16=False)
+    ref = PO.conv3x3(X.float().numpy(), Wt.float().numpy()) + bias.double().numpy()
+    assert _rel(Y.cpu().double().numpy(), ref) < TOL
+    # the image border (zero padding) is where a wrong shift would show
+    assert _rel(Y[:, 0].cpu().double().numpy(), ref[:, 0]) < TOL
+    assert _rel(Y[:, :, -1].cpu().double().numpy(), ref[:, :, -1]) < TOL
+
+
+def test_rejects_unsupported_shapes(P):
+    import torch
+    from paper_2512_12797_gb300 import _native
+    L = _native.lib()
+    A = torch.zeros((128, 64), dtype=torch.bfloat16, device="cuda")
+    D = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
+    assert L.prior_gemm_bf16(A.data_ptr(), A.data_ptr(), D.data_ptr(), 100, 128, 64, 128, 0, None, 0, None, None) == -1
+    assert L.prior_gemm_bf16(A.data_ptr(), A.data_ptr(), D.data_ptr(), 128, 48, 64, 128, 0, None, 0, None, None) == -1
+    assert L.prior_gemm_bf16(A.data_ptr(), A.data_ptr(), D.data_ptr(), 128, 128, 40, 128, 0, None, 0, None, None) == -1
+    X = torch.zeros((1, 16, 16, 32), dtype=torch.bfloat16, device="cuda")
+    assert L.prior_conv3x3_bf16(X.data_ptr(), X.data_ptr(), D.data_ptr(), 1, 16, 16, 32, 64, 0, None, 0, None,
+                                None) == -1

@@ -23,13 +23,14 @@ def native():
 
 
 def test_library_exports_every_declared_symbol(native):
-    hdr = open(os.path.join(ROOT, "include", "fwi.h")).read()
-    declared = set(re.findall(r"^(?:int|void|const char\*)\s+(\w+)\s*\(", hdr, re.M))
-    assert declared, "no declarations parsed"
-    assert declared == set(native.EXPORTS)
     L = native.lib()
-    for name in declared:
-        assert hasattr(L, name)
+    for header, exports in [("fwi.h", native.EXPORTS), ("prior.h", native.PRIOR_EXPORTS)]:
+        hdr = open(os.path.join(ROOT, "include", header)).read()
+        declared = set(re.findall(r"^(?:int|void|const char\*)\s+(\w+)\s*\(", hdr, re.M))
+        assert declared, "no declarations parsed in " + header
+        assert declared == set(exports), header
+        for name in declared:
+            assert hasattr(L, name)
 
 
 def test_encode_bit_exact_with_oracle(native):

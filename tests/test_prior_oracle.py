@@ -1,0 +1,57 @@
+"""Pins of oracle/prior_oracle.py (the FP64 definitions the learned prior's
+tensor-core kernels are checked against) against hand values and brute force."""
+import numpy as np
+
+from oracle import prior_oracle as PO
+
+
+def test_gemm_hand_values():
+    A = np.array([[1.0, 2.0, 3.0], [0.0, -1.0, 4.0]])
+    B = np.array([[1.0, 0.0, 0.0], [1.0, 1.0, 1.0], [2.0, -1.0, 0.5]])
+    expect = np.array([[1.0, 6.0, 1.5], [0.0, 3.0, 3.0]])  # row i of A . row j of B
+    assert np.array_equal(PO.gemm(A, B), expect)
+
+
+def _conv_brute(X, Wt):
+    n, H, W, C = X.shape
+    O = Wt.shape[0]
+    Y = np.zeros((n, H, W, O))
+    for b in range(n):
+        for y in range(H):
+            for x in range(W):
+                for o in range(O):
+                    acc = 0.0
+                    for dy in range(3):
+                        for dx in range(3):
+                            yy, xx = y + dy - 1, x + dx - 1
+                            if 0 <= yy < H and 0 <= xx < W:
+                                for c in range(C):
+                                    acc += Wt[o, dy * 3 + dx, c] * X[b, yy, xx, c]
+                    Y[b, y, x, o] = acc
+    return Y
+
+
+def test_conv3x3_matches_brute_force():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((2, 5, 4, 3))
+    Wt = rng.standard_normal((2, 9, 3))
+    assert np.allclose(PO.conv3x3(X, Wt), _conv_brute(X, Wt), rtol=0, atol=1e-12)
+
+
+def test_conv3x3_delta_reproduces_the_taps():
+    # a unit impulse at (y0, x0, c) reaches output (y0 - dy + 1, x0 - dx + 1) through tap (dy, dx)
+    X = np.zeros((1, 7, 7, 2))
+    X[0, 3, 3, 1] = 1.0
+    Wt = np.arange(2 * 9 * 2, dtype=float).reshape(2, 9, 2)
+    Y = PO.conv3x3(X, Wt)
+    for dy in range(3):
+        for dx in range(3):
+            assert np.array_equal(Y[0, 3 - dy + 1, 3 - dx + 1], Wt[:, dy * 3 + dx, 1])
+    assert np.count_nonzero(np.abs(Y).sum(-1)) == 9
+
+
+def test_conv3x3_zero_padding_on_constant_image():
+    X = np.ones((1, 4, 5, 1))
+    Wt = np.ones((1, 9, 1))
+    Y = PO.conv3x3(X, Wt)[0, :, :, 0]
+    assert Y[0, 0] == 4 and Y[0, 2] == 6 and Y[2, 2] == 9 and Y[3, 4] == 4
