@@ -402,11 +402,48 @@ def native_arm(args):
         ms_ck, _ = timed(step_ck, 2, 3000)
         out["checkpointed"] = {"value": units / (ms_ck * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_ck,
                                "budget_gb": args.checkpointed, "plan": ctx2.plan_info()}
+    if args.prior and world == 1 and w.ndim == 2:
+        out["prior"] = prior_measurement(w, nsamp, ms, peaks)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def prior_measurement(w, nsamp, ms_iter, peaks):
+    """The learned prior's x0-hat prediction on this batch's models, on the
+    tcgen05 kernels: time per call, the convolutions' algorithmic TFLOP/s
+    against the measured BF16 peak, and its cost next to one encoded Langevin
+    iteration.  (Random weights: the arithmetic does not depend on them.)"""
+    import torch
+    from paper_2512_12797_gb300 import unet
+    den = unet.UNetDenoiser(unet.init_params(0, out_scale=1.0))
+    Hp, Wp = unet.tile_shape(w.nz, w.nx)
+    flops = 0.0
+    for name, cin, cout in unet.LAYERS:
+        lev = {"e1": 0, "e2": 1, "ba": 2, "bb": 2, "d2": 1, "d1": 0}[name[:2]]
+        flops += 2.0 * (Hp >> lev) * (Wp >> lev) * 9 * ((cin + 63) // 64 * 64) * cout
+    flops = (flops + 2.0 * Hp * Wp * 64 * 32) * nsamp
+    x_t = torch.randn((nsamp, w.nz, w.nx), device="cuda")
+    for _ in range(3):
+        den(x_t, 0.5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 10
+    for _ in range(reps):
+        den(x_t, 0.5)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    return {"network": "U-Net 64/128/256, 3x3 convs on tcgen05 (BF16, FP32 accumulation)",
+            "input": [nsamp, w.nz, w.nx], "padded": [Hp, Wp], "ms_per_call": ms,
+            "conv_tflops": flops / (ms * 1e-3) / 1e12, "bf16_peak_tflops": peak,
+            "frac_of_peak": flops / (ms * 1e-3) / 1e12 / peak,
+            "share_of_langevin_iteration": ms / ms_iter,
+            "note": "whole call incl. padding, pooling, upsampling and concatenation (PyTorch tensor ops)"}
 
 
 def main():
@@ -421,6 +458,7 @@ def main():
                     help="also time the step with a pool of this many GB (forces recompute); 0 disables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler", type=int, default=1, help="also time one full-shot Langevin step (samples/hr)")
+    ap.add_argument("--prior", type=int, default=1, help="also time the learned prior's x0-hat prediction")
     ap.add_argument("--samples", type=int, default=0, help="override posterior samples (profiling runs)")
     ap.add_argument("--nt", type=int, default=0, help="override time steps (profiling runs)")
     ap.add_argument("--variants", default="", help="force step-kernel variants 'fwd,adj' (default: autotune)")
