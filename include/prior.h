@@ -28,8 +28,8 @@ enum prior_status {
 // D = A * B^T (+ bias) (ReLU if relu != 0).
 //   A: [M][K] BF16 row-major (K contiguous); B: [N][K] BF16 row-major;
 //   D: [M][ldd] FP32 (d_bf16 = 0) or BF16 (d_bf16 = 1); bias: [N] FP32 or null.
-// Requires M % 128 == 0, K % 64 == 0 and N in {32, 64, 128, 256} or
-// N % 128 == 0; ldd >= N and ldd % 8 == 0.
+// Requires M % 128 == 0, K % 64 == 0 and N in {32, 64, 128, 256} or a
+// multiple of 64; ldd >= N and ldd % 8 == 0.
 int prior_gemm_bf16(const void* A, const void* B, void* D, int M, int N, int K, int ldd, int d_bf16,
                     const float* bias, int relu, int* status, void* stream);
 
@@ -38,10 +38,25 @@ int prior_gemm_bf16(const void* A, const void* B, void* D, int M, int N, int K, 
 //   Y[n][y][x][o] = sum_{dy,dx in 0..2} sum_c Wt[o][dy*3+dx][c] * X[n][y+dy-1][x+dx-1][c].
 //   X: [nimg][H][W][Cin] BF16 (NHWC); Wt: [Cout][9][Cin] BF16;
 //   Y: [nimg][H][W][Cout] FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1); bias: [Cout] FP32 or null.
-// Requires Cin % 64 == 0; Cout in {32, 64, 128, 256} or Cout % 128 == 0;
+// Requires Cin % 64 == 0; Cout in {32, 64, 128, 256} or a multiple of 64;
 // W a power of two <= 128 or a multiple of 128; H * min(W, 128) a multiple of 128.
+// The data gradient of this layer is the same call on the output gradient
+// with weights Wt'[c][8 - t][o] = Wt[o][t][c].
 int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, int W, int Cin, int Cout,
                        int y_bf16, const float* bias, int relu, int* status, void* stream);
+
+// Weight gradient of prior_conv3x3_bf16, accumulated:
+//   dW[o][t][c] += sum_p dYt[o][p] * X9[t][c][p],
+// where X9[t][c][p] = X[n][y+dy-1][x+dx-1][c] (zero off the image) for pixel
+// p = (n, y, x) and tap t = dy*3 + dx, i.e. the input's tap-shifted copies.
+//   dYt: [ceil(Cout/128)*128][P] BF16 (channel-major output gradient; rows
+//        >= Cout are read but not used); X9: [9][Cin][P] BF16;
+//   dW: [Cout][9][Cin] FP32, accumulated with atomic adds (zero it first).
+// The pixels are split into `splits` ranges per tap for parallelism; the sum
+// order therefore varies between runs.  Requires P % 64 == 0 and Cin in
+// {32, 64, 128, 256} or a multiple of 64.
+int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
+                             int* status, void* stream);
 
 // Reads and clears the internal status word (synchronises the stream).
 int prior_last_status(void* stream);

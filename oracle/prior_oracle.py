@@ -30,3 +30,34 @@ def conv3x3(X, Wt):
             # tap (dy, dx) reads the input shifted by (dy - 1, dx - 1)
             Y += Xp[:, dy:dy + H, dx:dx + W, :] @ Wt[:, dy * 3 + dx, :].T
     return Y
+
+
+def conv3x3_dgrad(dY, Wt):
+    """Input gradient of conv3x3, written as the scatter of every output
+    gradient back through the nine taps: dX[n, y+dy-1, x+dx-1, c] +=
+    sum_o dY[n, y, x, o] Wt[o, dy*3+dx, c] (contributions off the image dropped)."""
+    dY = np.asarray(dY, np.float64)
+    Wt = np.asarray(Wt, np.float64)
+    n, H, W, O = dY.shape
+    C = Wt.shape[2]
+    dXp = np.zeros((n, H + 2, W + 2, C))
+    for dy in range(3):
+        for dx in range(3):
+            dXp[:, dy:dy + H, dx:dx + W, :] += dY @ Wt[:, dy * 3 + dx, :]
+    return dXp[:, 1:H + 1, 1:W + 1, :]
+
+
+def conv3x3_wgrad(dY, X):
+    """Weight gradient of conv3x3: dW[o, dy*3+dx, c] = sum over pixels of
+    dY[n, y, x, o] X[n, y+dy-1, x+dx-1, c] (zero off the image)."""
+    dY = np.asarray(dY, np.float64)
+    X = np.asarray(X, np.float64)
+    n, H, W, O = dY.shape
+    C = X.shape[3]
+    Xp = np.zeros((n, H + 2, W + 2, C))
+    Xp[:, 1:H + 1, 1:W + 1, :] = X
+    dW = np.zeros((O, 9, C))
+    for dy in range(3):
+        for dx in range(3):
+            dW[:, dy * 3 + dx, :] = dY.reshape(-1, O).T @ Xp[:, dy:dy + H, dx:dx + W, :].reshape(-1, C)
+    return dW

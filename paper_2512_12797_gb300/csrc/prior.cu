@@ -80,6 +80,20 @@ __device__ __forceinline__ void tma4d(void* dst, const CUtensorMap* m, int c0, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* m, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
+      : "memory");
+}
+
+// Kernel modes: plain GEMM; 3x3 convolution (forward, and data gradient with
+// flipped weights); weight gradient of the 3x3 convolution: per tap a GEMM
+// over pixels, dY^T [Cout x P] times the tap-shifted input [Cin x P]^T, split
+// over pixel ranges and accumulated atomically in FP32.
+enum Mode { GEMM = 0, CONV = 1, WGRAD = 2 };
+
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA with
 // the 128-byte swizzle: rows of 64 BF16 (128 B), 8-row swizzle atoms 1024 B
 // apart (stride byte offset), descriptor version 1, layout "128-byte swizzle".
@@ -148,6 +162,7 @@ struct Args {
   const float* bias; // [N] or null
   int relu;
   int H, W, Cin, TW, TH;  // convolution geometry (tile = TH rows x TW columns of one image)
+  int splits;        // weight gradient: pixel ranges per tap (grid z = 9 * splits)
   int* status;
 };
 
@@ -160,7 +175,7 @@ struct Smem {
   static constexpr int bytes = OFF_BAR + (2 * STAGES + 2) * 8 + 16 + 1024;  // + alignment slack
 };
 
-template <int BN, int STAGES, bool CONV>
+template <int BN, int STAGES, int MODE>
 __global__ void __launch_bounds__(128, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b, const Args g) {
   using S = Smem<BN, STAGES>;
@@ -175,7 +190,14 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = g.K / BK;
+  // K blocks of this CTA: all of K, or (weight gradient) this split's 64-pixel chunks
+  int kb0 = 0, nk = g.K / BK, tap = 0;
+  if (MODE == WGRAD) {
+    tap = blockIdx.z % 9;
+    const int split = blockIdx.z / 9, chunks = g.K / BK;
+    kb0 = (int)((long long)chunks * split / g.splits);
+    nk = (int)((long long)chunks * (split + 1) / g.splits) - kb0;
+  }
 
   if (tid == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_a)) : "memory");
@@ -201,7 +223,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
 
   // convolution tile: TH rows x TW columns of image img starting at (y0, x0)
   int img = 0, y0 = 0, x0 = 0, ncb = 1;
-  if (CONV) {
+  if (MODE == CONV) {
     const int hw = g.H * g.W;
     img = m0 / hw;
     const int rem = m0 - img * hw;
@@ -217,14 +239,20 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
       if (kb >= STAGES && !mbar_wait(&empty[s], (uint32_t)((kb / STAGES - 1) & 1), g.status, abort_flag)) break;
       unsigned char* st = sm + s * S::STAGE;
       mbar_expect_tx(&full[s], S::STAGE);
-      if (CONV) {
-        const int tap = kb / ncb, cb = kb - tap * ncb;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      if (MODE == CONV) {
+        const int t = kb / ncb, cb = kb - t * ncb;
+        const int dy = t / 3 - 1, dx = t % 3 - 1;
         tma4d(st, &tma_a, cb * BK, x0 + dx, y0 + dy, img, &full[s]);
+        tma2d(st + S::A_BYTES, &tma_b, kb * BK, n0, &full[s]);
+      } else if (MODE == WGRAD) {
+        // 64-pixel chunk p0: dY^T rows m0.. and the tap's shifted input rows n0..
+        const int p0 = (kb0 + kb) * BK;
+        tma2d(st, &tma_a, p0, m0, &full[s]);
+        tma3d(st + S::A_BYTES, &tma_b, p0, n0, tap, &full[s]);
       } else {
         tma2d(st, &tma_a, kb * BK, m0, &full[s]);
+        tma2d(st + S::A_BYTES, &tma_b, kb * BK, n0, &full[s]);
       }
-      tma2d(st + S::A_BYTES, &tma_b, kb * BK, n0, &full[s]);
     }
     if (kb < nk) {  // aborted: bounded wait for the copies in flight
       for (int i = kb - STAGES > 0 ? kb - STAGES : 0; i < kb; i++) {
@@ -266,7 +294,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
           if (g.relu) x = fmaxf(x, 0.f);
           v[i] = x;
         }
-        if (g.d_bf16) {
+        if (MODE == WGRAD) {
+          float* d = reinterpret_cast<float*>(g.D) + (long long)row * g.ldd + tap * g.Cin + n0 + c0;
+#pragma unroll
+          for (int i = 0; i < 32; i++) atomicAdd(d + i, v[i]);
+        } else if (g.d_bf16) {
           __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(g.D) + (long long)row * g.ldd + n0 + c0;
 #pragma unroll
           for (int i = 0; i < 32; i += 8)
@@ -333,36 +365,37 @@ int* status_ptr(int* status) {
   return cudaGetSymbolAddress(&p, g_prior_status) == cudaSuccess ? reinterpret_cast<int*>(p) : nullptr;
 }
 
-template <int BN, bool CONV>
+template <int BN, int MODE>
 int launch(const CUtensorMap& ma, const CUtensorMap& mb, const prior::Args& g, cudaStream_t st) {
   constexpr int STAGES = BN >= 256 ? 3 : 4;
   using S = prior::Smem<BN, STAGES>;
-  auto kern = prior::gemm_kernel<BN, STAGES, CONV>;
+  auto kern = prior::gemm_kernel<BN, STAGES, MODE>;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::bytes) != cudaSuccess)
       return PRIOR_ERR_CUDA;
     attr = true;
   }
-  dim3 grid(g.M / prior::BM, g.N / BN);
+  dim3 grid((g.M + prior::BM - 1) / prior::BM, g.N / BN, MODE == prior::WGRAD ? 9 * g.splits : 1);
   kern<<<grid, 128, S::bytes, st>>>(ma, mb, g);
   return cudaGetLastError() == cudaSuccess ? PRIOR_OK : PRIOR_ERR_CUDA;
 }
 
-template <bool CONV>
+template <int MODE>
 int dispatch(int bn, const CUtensorMap& ma, const CUtensorMap& mb, const prior::Args& g, cudaStream_t st) {
   switch (bn) {
-    case 32: return launch<32, CONV>(ma, mb, g, st);
-    case 64: return launch<64, CONV>(ma, mb, g, st);
-    case 128: return launch<128, CONV>(ma, mb, g, st);
-    case 256: return launch<256, CONV>(ma, mb, g, st);
+    case 32: return launch<32, MODE>(ma, mb, g, st);
+    case 64: return launch<64, MODE>(ma, mb, g, st);
+    case 128: return launch<128, MODE>(ma, mb, g, st);
+    case 256: return launch<256, MODE>(ma, mb, g, st);
   }
   return PRIOR_ERR_ARG;
 }
 
 int tile_n(int N) {
   if (N == 32 || N == 64 || N == 128 || N == 256) return N;
-  return N > 0 && N % 128 == 0 ? 128 : 0;
+  if (N > 0 && N % 128 == 0) return 128;
+  return N > 0 && N % 64 == 0 ? 64 : 0;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -393,7 +426,7 @@ int prior_gemm_bf16(const void* A, const void* B, void* D, int M, int N, int K, 
   const cuuint64_t da[2] = {(cuuint64_t)K, (cuuint64_t)M}, db[2] = {(cuuint64_t)K, (cuuint64_t)N};
   const cuuint32_t ba[2] = {prior::BK, prior::BM}, bb[2] = {prior::BK, (cuuint32_t)bn};
   if (!make_map(&ma, A, 2, da, ba) || !make_map(&mb, B, 2, db, bb)) return PRIOR_ERR_ARG;
-  return dispatch<false>(bn, ma, mb, g, (cudaStream_t)stream);
+  return dispatch<prior::GEMM>(bn, ma, mb, g, (cudaStream_t)stream);
 }
 
 int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, int W, int Cin, int Cout,
@@ -427,7 +460,33 @@ int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, 
   const cuuint64_t db[2] = {(cuuint64_t)(9 * Cin), (cuuint64_t)Cout};
   const cuuint32_t bb[2] = {prior::BK, (cuuint32_t)bn};
   if (!make_map(&ma, X, 4, da, ba) || !make_map(&mb, Wt, 2, db, bb)) return PRIOR_ERR_ARG;
-  return dispatch<true>(bn, ma, mb, g, (cudaStream_t)stream);
+  return dispatch<prior::CONV>(bn, ma, mb, g, (cudaStream_t)stream);
+}
+
+int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
+                             int* status, void* stream) {
+  const int bn = tile_n(Cin);
+  const int mp = (Cout + prior::BM - 1) / prior::BM * prior::BM;
+  if (!dYt || !X9 || !dW || P <= 0 || P % prior::BK || Cout <= 0 || !bn || splits < 1 || splits > 4096)
+    return PRIOR_ERR_ARG;
+  if (!aligned16(dYt) || !aligned16(X9) || !aligned16(dW)) return PRIOR_ERR_ARG;
+  prior::Args g = {};
+  g.M = Cout;
+  g.N = Cin;
+  g.K = P;
+  g.ldd = 9 * Cin;
+  g.D = dW;
+  g.Cin = Cin;
+  g.splits = splits < P / prior::BK ? splits : P / prior::BK;
+  g.status = status_ptr(status);
+  if (!g.status) return PRIOR_ERR_CUDA;
+  CUtensorMap ma, mb;
+  const cuuint64_t da[2] = {(cuuint64_t)P, (cuuint64_t)mp};
+  const cuuint32_t ba[2] = {prior::BK, prior::BM};
+  const cuuint64_t db[3] = {(cuuint64_t)P, (cuuint64_t)Cin, 9};
+  const cuuint32_t bb[3] = {prior::BK, (cuuint32_t)bn, 1};
+  if (!make_map(&ma, dYt, 2, da, ba) || !make_map(&mb, X9, 3, db, bb)) return PRIOR_ERR_ARG;
+  return dispatch<prior::WGRAD>(bn, ma, mb, g, (cudaStream_t)stream);
 }
 
 int prior_last_status(void* stream) {

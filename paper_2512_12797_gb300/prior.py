@@ -52,3 +52,48 @@ def conv3x3(X, Wt, bias=None, relu=False, out_bf16=True, out=None):
 def last_status():
     """Device status word of the prior kernels (read and cleared)."""
     return _native.lib().prior_last_status(_stream())
+
+
+def flip_weights(Wt):
+    """Weights of the data gradient: Wt'[c][8 - t][o] = Wt[o][t][c]."""
+    return Wt.flip(1).transpose(0, 2).contiguous()
+
+
+def conv3x3_dgrad(dY, Wt, out_bf16=True):
+    """Gradient of conv3x3 with respect to its input: the same-size
+    convolution of dY [n, H, W, Cout] with the flipped, transposed weights."""
+    return conv3x3(dY, flip_weights(Wt), out_bf16=out_bf16)
+
+
+def shifted_taps(X):
+    """[9][Cin][P] BF16: X [n, H, W, Cin] shifted by (dy - 1, dx - 1) for each
+    tap t = dy*3 + dx, zero off the image, channel-major over pixels P = n*H*W."""
+    n, H, W, C = X.shape
+    Xp = torch.nn.functional.pad(X.permute(3, 0, 1, 2), (1, 1, 1, 1))  # [C, n, H+2, W+2]
+    out = torch.empty((9, C, n * H * W), dtype=X.dtype, device=X.device)
+    for dy in range(3):
+        for dx in range(3):
+            out[dy * 3 + dx] = Xp[:, :, dy:dy + H, dx:dx + W].reshape(C, -1)
+    return out
+
+
+def conv3x3_wgrad(dY, X, splits=None, out=None):
+    """Gradient of conv3x3 with respect to its weights: dW [Cout, 9, Cin] FP32
+    from the output gradient dY [n, H, W, Cout] and the input X [n, H, W, Cin]."""
+    n, H, W, Cout = dY.shape
+    Cin = X.shape[-1]
+    P = n * H * W
+    mp = (Cout + 127) // 128 * 128
+    dYt = torch.zeros((mp, P), dtype=torch.bfloat16, device=dY.device)
+    dYt[:Cout] = dY.reshape(P, Cout).t()
+    X9 = shifted_taps(X.to(torch.bfloat16))
+    if out is None:
+        out = torch.zeros((Cout, 9, Cin), dtype=torch.float32, device=dY.device)
+    if splits is None:  # about two CTAs per SM over the (co, ci, tap) tiles
+        bn = Cin if Cin in (32, 64, 128, 256) else (128 if Cin % 128 == 0 else 64)
+        tiles = ((Cout + 127) // 128) * (Cin // bn) * 9
+        splits = max(1, min(P // 64, (2 * 152) // tiles))
+    rc = _native.lib().prior_conv3x3_wgrad_bf16(dYt.data_ptr(), X9.data_ptr(), out.data_ptr(), P, Cout, Cin,
+                                                splits, None, _stream())
+    _check(rc, "prior_conv3x3_wgrad_bf16")
+    return out

@@ -77,3 +77,25 @@ def test_rejects_unsupported_shapes(P):
     X = torch.zeros((1, 16, 16, 32), dtype=torch.bfloat16, device="cuda")
     assert L.prior_conv3x3_bf16(X.data_ptr(), X.data_ptr(), D.data_ptr(), 1, 16, 16, 32, 64, 0, None, 0, None,
                                 None) == -1
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", [(2, 16, 16, 64, 64), (1, 32, 64, 192, 128), (2, 8, 16, 128, 384)])
+def test_conv3x3_dgrad_matches_oracle(P, n, H, W, Cin, Cout):
+    import torch
+    dY, Wt = _bf16(torch, (n, H, W, Cout), 21 + H), _bf16(torch, (Cout, 9, Cin), 22 + Cin)
+    dX = P.conv3x3_dgrad(dY.cuda(), Wt.cuda(), out_bf16=False)
+    ref = PO.conv3x3_dgrad(dY.float().numpy(), Wt.float().numpy())
+    assert _rel(dX.cpu().double().numpy(), ref) < TOL
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", [(2, 16, 16, 64, 64), (1, 32, 32, 128, 256), (4, 8, 8, 64, 32),
+                                            (1, 16, 64, 192, 128)])
+def test_conv3x3_wgrad_matches_oracle(P, n, H, W, Cin, Cout):
+    import torch
+    dY, X = _bf16(torch, (n, H, W, Cout), 31 + W), _bf16(torch, (n, H, W, Cin), 32 + Cout)
+    dW = P.conv3x3_wgrad(dY.cuda(), X.cuda())
+    ref = PO.conv3x3_wgrad(dY.float().numpy(), X.float().numpy())
+    assert _rel(dW.cpu().double().numpy(), ref) < 1e-4
+    # the tap layout: the centre tap alone is the plain channel correlation
+    assert _rel(dW[:, 4].cpu().double().numpy(), ref[:, 4]) < 1e-4
+    assert P.last_status() == 0

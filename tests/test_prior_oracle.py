@@ -55,3 +55,30 @@ def test_conv3x3_zero_padding_on_constant_image():
     Wt = np.ones((1, 9, 1))
     Y = PO.conv3x3(X, Wt)[0, :, :, 0]
     assert Y[0, 0] == 4 and Y[0, 2] == 6 and Y[2, 2] == 9 and Y[3, 4] == 4
+
+
+def test_conv_gradients_satisfy_the_adjoint_identities():
+    # <conv(X, W), G> = <X, dgrad(G, W)> = <W, wgrad(G, X)>: the conv is bilinear
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((2, 6, 5, 3))
+    Wt = rng.standard_normal((4, 9, 3))
+    G = rng.standard_normal((2, 6, 5, 4))
+    lhs = float(np.sum(PO.conv3x3(X, Wt) * G))
+    assert abs(lhs - float(np.sum(X * PO.conv3x3_dgrad(G, Wt)))) < 1e-10 * max(1.0, abs(lhs))
+    assert abs(lhs - float(np.sum(Wt * PO.conv3x3_wgrad(G, X)))) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_conv_gradients_match_finite_differences():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((1, 4, 4, 2))
+    Wt = rng.standard_normal((2, 9, 2))
+    G = rng.standard_normal((1, 4, 4, 2))
+    loss = lambda X_, W_: float(np.sum(_conv_brute(X_, W_) * G))
+    dX, dW = PO.conv3x3_dgrad(G, Wt), PO.conv3x3_wgrad(G, X)
+    e = 1e-6
+    for idx in [(0, 0, 0, 0), (0, 3, 2, 1), (0, 1, 3, 0)]:
+        Xe = X.copy(); Xe[idx] += e
+        assert abs((loss(Xe, Wt) - loss(X, Wt)) / e - dX[idx]) < 1e-5
+    for idx in [(0, 0, 0), (1, 4, 1), (0, 8, 1)]:
+        We = Wt.copy(); We[idx] += e
+        assert abs((loss(X, We) - loss(X, Wt)) / e - dW[idx]) < 1e-5
