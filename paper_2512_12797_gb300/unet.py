@@ -117,6 +117,87 @@ def forward_tc(q, y, sigma):
     return y + o + bo
 
 
+def _unpool(g):  # adjoint of the 2 x 2 average pool (NHWC)
+    return (0.25 * g.float()).repeat_interleave(2, 1).repeat_interleave(2, 2)
+
+
+def _downsum(g):  # adjoint of the nearest x 2 upsample (NHWC)
+    n, H, W, C = g.shape
+    return g.float().view(n, H // 2, 2, W // 2, 2, C).sum((2, 4))
+
+
+def forward_tc_train(q, y, sigma):
+    """forward_tc keeping what the backward pass needs: each conv layer's input
+    and (post-ReLU) output, BF16 NHWC."""
+    n, H, W = y.shape
+    x = torch.zeros((n, H, W, 64), dtype=torch.bfloat16, device=y.device)
+    x[..., 0] = y.to(torch.bfloat16)
+    x[..., 1] = sigma.view(n, 1, 1).to(torch.bfloat16)
+    saved = {}
+
+    def c(h, name):
+        w, b = q[name]
+        out = TC.conv3x3(h, w, bias=b, relu=True)
+        saved[name] = (h, out)
+        return out
+
+    h = c(x, "e1a")
+    e1 = c(h, "e1b")
+    h = c(_pool(e1), "e2a")
+    e2 = c(h, "e2b")
+    h = c(_pool(e2), "ba")
+    h = c(h, "bb")
+    h = c(torch.cat([_up(h), e2], -1).contiguous(), "d2a")
+    h = c(h, "d2b")
+    h = c(torch.cat([_up(h), e1], -1).contiguous(), "d1a")
+    h = c(h, "d1b")
+    wo, bo = q["out"]
+    o = TC.gemm_bf16(h.view(-1, 64), wo)[:, 0].view(n, H, W)
+    return y + o + bo, saved
+
+
+def backward_tc(q, saved, g):
+    """Gradients of sum(g * x0-hat) with respect to the parameters, with every
+    3x3 convolution's data and weight gradient on the tcgen05 kernels (BF16
+    operands, FP32 accumulation; gradients kept in FP32 between layers).  Returns {name.w: [Cout, Cin, 3, 3],
+    name.b: [Cout], out.w, out.b} in FP32, the layout of init_params."""
+    grads = {}
+    h = saved["d1b"][1]
+    n, H, W, _ = h.shape
+    gf = g.float().reshape(-1)
+    wo = q["out"][0][0].float()
+    grads["out.w"] = (h.view(-1, 64).float().t() @ gf).view(1, 64, 1, 1)
+    grads["out.b"] = gf.sum().view(1)
+    dh = g.float()[..., None] * wo  # [n, H, W, 64]
+
+    def layer(name, d_out, need_dx=True):
+        # gradients stay FP32 between layers; BF16 only as convolution operands
+        x, a = saved[name]
+        dzf = d_out.float() * (a > 0)  # through the ReLU
+        dz = dzf.to(torch.bfloat16).contiguous()
+        cin = dict((l[0], l[1]) for l in LAYERS)[name]
+        grads[name + ".b"] = dzf.sum((0, 1, 2))
+        dw = TC.conv3x3_wgrad(dz, x)  # [Cout, 9, Cin']
+        grads[name + ".w"] = dw[:, :, :cin].reshape(dw.shape[0], 3, 3, cin).permute(0, 3, 1, 2).contiguous()
+        return TC.conv3x3_dgrad(dz, q[name][0], out_bf16=False) if need_dx else None
+
+    d = layer("d1b", dh)
+    d = layer("d1a", d)                       # [.., 192] = up(d2b out) | e1
+    d_up1, d_e1 = d[..., :128], d[..., 128:]
+    d = layer("d2b", _downsum(d_up1))
+    d = layer("d2a", d)                       # [.., 384] = up(bb out) | e2
+    d_up2, d_e2 = d[..., :256], d[..., 256:]
+    d = layer("bb", _downsum(d_up2))
+    d = layer("ba", d)
+    d_e2 = d_e2 + _unpool(d)
+    d = layer("e2b", d_e2)
+    d = layer("e2a", d)
+    d_e1 = d_e1 + _unpool(d)
+    d = layer("e1b", d_e1)
+    layer("e1a", d, need_dx=False)
+    return grads
+
+
 def _width_ok(w):
     for lev in range(3):
         if w % (1 << lev):
@@ -145,9 +226,14 @@ def tile_shape(H, W):
     return Hp, Wp
 
 
-def train(p, patches, steps, batch=64, lr=2e-3, sigma_range=(0.02, 3.0), seed=0, log_every=0):
+def train(p, patches, steps, batch=64, lr=2e-3, sigma_range=(0.02, 3.0), seed=0, log_every=0, backend="torch"):
     """Adam on E || x0-hat(x0 + sigma eps, sigma) - x0 ||^2 with sigma
-    log-uniform in sigma_range, over FP32 patches [N, S, S] on the device."""
+    log-uniform in sigma_range, over FP32 patches [N, S, S] on the device.
+    backend "torch": PyTorch convolutions and autograd in FP32; "tc": forward
+    and backward convolutions on the tcgen05 kernels (BF16 activations and
+    gradients, FP32 accumulation and FP32 master weights)."""
+    if backend == "tc":
+        return _train_tc(p, patches, steps, batch, lr, sigma_range, seed, log_every)
     for v in p.values():
         v.requires_grad_(True)
     opt = torch.optim.Adam(list(p.values()), lr=lr)
@@ -169,6 +255,33 @@ def train(p, patches, steps, batch=64, lr=2e-3, sigma_range=(0.02, 3.0), seed=0,
             hist.append(float(loss.detach()))
     for v in p.values():
         v.requires_grad_(False)
+    return hist
+
+
+def _train_tc(p, patches, steps, batch, lr, sigma_range, seed, log_every):
+    keys = list(p.keys())
+    opt = torch.optim.Adam([p[k] for k in keys], lr=lr)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, steps)
+    g = torch.Generator(device=patches.device).manual_seed(seed)
+    lo, hi = math.log(sigma_range[0]), math.log(sigma_range[1])
+    hist = []
+    for k in range(steps):
+        idx = torch.randint(0, patches.shape[0], (batch,), device=patches.device, generator=g)
+        x0 = patches[idx]
+        sig = torch.exp(lo + (hi - lo) * torch.rand(batch, device=patches.device, generator=g))
+        y = (x0 + sig.view(-1, 1, 1) * torch.randn(x0.shape, device=patches.device, generator=g)).contiguous()
+        q = pack(p)
+        xh, saved = forward_tc_train(q, y, sig)
+        r = xh - x0
+        grads = backward_tc(q, saved, (2.0 / r.numel()) * r)  # d mean(r^2)
+        for key in keys:
+            p[key].grad = grads[key].view_as(p[key])
+        opt.step()
+        sched.step()
+        if log_every and k % log_every == 0:
+            hist.append(float((r * r).mean()))
+    for key in keys:
+        p[key].grad = None
     return hist
 
 

@@ -66,3 +66,63 @@ def test_trained_prior_beats_gaussian_and_no_prior(U):
         e_gauss = float(((gauss(x_t, abar) - held) ** 2).mean())
         assert e_unet < 0.7 * e_gauss, (sigma, e_unet, e_gauss)
         assert e_unet < 0.3 * sigma * sigma, (sigma, e_unet)
+
+
+def test_tc_backward_matches_autograd(U):
+    # Gradients of sum(g * x0-hat) on the tcgen05 kernels against autograd of
+    # the BF16-rounding reference.  The two forwards already differ by ~1e-2
+    # (accumulation order, and the BF16 roundings and ReLU decisions that it
+    # flips); ten layers of backpropagation amplify that, most in the bias
+    # gradients (sums over all pixels with heavy cancellation).  Agreement is
+    # therefore a few percent in norm with the direction kept (cosine > 0.99),
+    # while a wiring mistake (channel split, skip, pooling adjoint) shows up as
+    # an O(1) error.  The kernels themselves are checked against the FP64
+    # oracle in test_gpu_prior.
+    import torch
+    p = U.init_params(5, out_scale=8.0)
+    gen = torch.Generator().manual_seed(6)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = 0.1 * torch.randn(p[k].shape, generator=gen).cuda()
+    x0 = torch.tensor(SP.geology_patches(4, 64, 7)).cuda()
+    sig = torch.tensor([0.1, 0.3, 0.7, 1.5]).cuda()
+    y = (x0 + sig.view(-1, 1, 1) * torch.randn(x0.shape, generator=gen).cuda()).contiguous()
+    g = torch.randn(y.shape, generator=gen).cuda()
+    rnd = lambda t: t.to(torch.bfloat16).float()
+    pb = {k: (rnd(v) if k.endswith(".w") else v).clone().requires_grad_(True) for k, v in p.items()}
+    (U.forward_torch(pb, y, sig, act_round=rnd) * g).sum().backward()
+    q = U.pack(p)
+    _, saved = U.forward_tc_train(q, y, sig)
+    grads = U.backward_tc(q, saved, g)
+    worst = []
+    for k, v in pb.items():
+        ref = v.grad
+        got = grads[k].view_as(ref)
+        rel = float((got - ref).norm() / ref.norm().clamp_min(1e-30))
+        cos = float((got * ref).sum() / (got.norm() * ref.norm()).clamp_min(1e-30))
+        worst.append((rel, cos, k))
+    print("tcgen05 backward vs autograd, worst (rel, cos, name):", max(worst), min(worst, key=lambda w: w[1]))
+    for rel, cos, k in worst:
+        assert rel < 0.15 and cos > 0.99, (k, rel, cos)
+        if k.endswith(".w"):
+            assert rel < 0.1 and cos > 0.995, (k, rel, cos)
+
+
+def test_training_on_tcgen05_kernels_beats_gaussian(U):
+    import torch
+    from paper_2512_12797_gb300.sampler import GaussianPriorDenoiser
+    train_set = torch.tensor(SP.geology_patches(8192, 64, 12)).cuda()
+    p = U.init_params(1)
+    hist = U.train(p, train_set, steps=800, batch=64, lr=2e-3, seed=2, log_every=100, backend="tc")
+    assert hist[-1] < hist[0]
+    held = torch.tensor(SP.geology_patches(256, 64, 98)).cuda()
+    den = U.UNetDenoiser(p)
+    mean = torch.full((64, 64), float(train_set.mean()), device="cuda")
+    gauss = GaussianPriorDenoiser(mean, corr_cells=6.0, amp=float(train_set.std()))
+    gen = torch.Generator(device="cuda").manual_seed(8)
+    for sigma in (0.2, 0.5, 1.0):
+        abar = 1.0 / (1.0 + sigma * sigma)
+        x_t = math.sqrt(abar) * (held + sigma * torch.randn(held.shape, device="cuda", generator=gen))
+        e_unet = float(((den(x_t, abar) - held) ** 2).mean())
+        e_gauss = float(((gauss(x_t, abar) - held) ** 2).mean())
+        assert e_unet < 0.7 * e_gauss, (sigma, e_unet, e_gauss)
