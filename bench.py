@@ -338,7 +338,10 @@ def native_arm(args):
                    "ms_per_step": ms_e2e},
            "gpu_launches": int(phase_launch.sum() + n * 2),
            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak,
+                        "traffic": (committed_traffic(dom) if w.name == "thrust2d" and nsamp == 16
+                                    and plan["samples_per_chunk"] == nsamp else None),
+                        "traffic_unit": "bytes per step (dram read + write, ncu, profiles/step2d_thrust2d_traffic.md)",
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
                         "bytes_per_update": bpu["adjoint" if "ADJ" in dom else "forward"],
                         "avg_step_ms": kern[dom]["ms"],
@@ -409,6 +412,24 @@ def native_arm(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def committed_traffic(kernel_name):
+    """DRAM bytes per step of the named step kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        src = open(os.path.join(here, "paper_2512_12797_gb300", "csrc", "stencil.cu"), "rb").read()
+        txt = open(os.path.join(here, "profiles", "step2d_thrust2d_traffic.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic-key stencil.cu sha256=([0-9a-f]+) forward_bytes_per_step=(\d+) "
+                  r"adjoint_bytes_per_step=(\d+)", txt)
+    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    return float(m.group(3) if "ADJ" in kernel_name else m.group(2))
 
 
 def prior_measurement(w, nsamp, ms_iter, peaks):

@@ -176,7 +176,7 @@ struct Smem {
 };
 
 template <int BN, int STAGES, int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
 gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b, const Args g) {
   using S = Smem<BN, STAGES>;
   constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
@@ -367,7 +367,7 @@ int* status_ptr(int* status) {
 
 template <int BN, int MODE>
 int launch(const CUtensorMap& ma, const CUtensorMap& mb, const prior::Args& g, cudaStream_t st) {
-  constexpr int STAGES = BN >= 256 ? 3 : 4;
+  constexpr int STAGES = 3;  // 96 KB at BN = 128: two CTAs per SM overlap one's epilogue with the other's MMAs
   using S = prior::Smem<BN, STAGES>;
   auto kern = prior::gemm_kernel<BN, STAGES, MODE>;
   static bool attr = false;

@@ -97,3 +97,31 @@ def conv3x3_wgrad(dY, X, splits=None, out=None):
                                                 splits, None, _stream())
     _check(rc, "prior_conv3x3_wgrad_bf16")
     return out
+
+
+def _main():
+    """Times one 3x3 convolution: python -m paper_2512_12797_gb300.prior [n H W Cin Cout]."""
+    import sys
+    from . import build
+    build.build()
+    n, H, W, Cin, Cout = [int(a) for a in sys.argv[1:6]] if len(sys.argv) > 5 else (16, 128, 128, 128, 128)
+    X = torch.randn(n, H, W, Cin, device="cuda").to(torch.bfloat16)
+    Wt = torch.randn(Cout, 9, Cin, device="cuda").to(torch.bfloat16)
+    Y = torch.empty(n, H, W, Cout, device="cuda", dtype=torch.bfloat16)
+    for _ in range(3):
+        conv3x3(X, Wt, out=Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        conv3x3(X, Wt, out=Y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    flops = 2.0 * n * H * W * 9 * Cin * Cout
+    print("conv3x3 [%d, %d, %d, %d] -> %d: %.3f ms, %.0f TFLOP/s, status %d"
+          % (n, H, W, Cin, Cout, ms, flops / ms / 1e9, last_status()))
+
+
+if __name__ == "__main__":
+    _main()
