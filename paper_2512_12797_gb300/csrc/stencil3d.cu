@@ -44,9 +44,15 @@ __device__ __forceinline__ float comp(const float4& v, int j) {
   return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 0 ? f2(v.x, v.y) : f2(v.z, v.w); }
+
 // Laplacian of the thread's 4 points: x and y neighbours from the halo plane H
 // (row ly+4, columns lx..lx+11), z neighbours from the circular register queue
 // Q (Q[(C+k) % 9] holds level z+k, k = -4..4, C the index of the centre).
+// Adjacent columns are computed as pairs with the packed FP32 instructions;
+// each point sees the operations of the scalar form in the same order
+// (x - y as fma(y, -1, x), exact).
 template <int C>
 __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[9], int ly, int lx,
                                      const Coef& K, float (&lap)[4]) {
@@ -60,22 +66,28 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
     yn[k - 1] = ld4s(H + (ly + HALO - k) * HX + lx + 4);
     yn[k + 3] = ld4s(H + (ly + HALO + k) * HX + lx + 4);
   }
+  const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
-  for (int j = 0; j < 4; j++) {
-    const float p = w[4 + j], p2 = p + p;
-    float a = K.cx[4] * ((w[8 + j] + w[j]) - p2);
-    a = fmaf(K.cx[3], (w[7 + j] + w[1 + j]) - p2, a);
-    a = fmaf(K.cx[2], (w[6 + j] + w[2 + j]) - p2, a);
-    a = fmaf(K.cx[1], (w[5 + j] + w[3 + j]) - p2, a);
-    a = fmaf(K.cy[4], (comp(yn[7], j) + comp(yn[3], j)) - p2, a);
-    a = fmaf(K.cy[3], (comp(yn[6], j) + comp(yn[2], j)) - p2, a);
-    a = fmaf(K.cy[2], (comp(yn[5], j) + comp(yn[1], j)) - p2, a);
-    a = fmaf(K.cy[1], (comp(yn[4], j) + comp(yn[0], j)) - p2, a);
-    a = fmaf(K.cz[4], (comp(Q[(C + 4) % 9], j) + comp(Q[(C + 5) % 9], j)) - p2, a);
-    a = fmaf(K.cz[3], (comp(Q[(C + 3) % 9], j) + comp(Q[(C + 6) % 9], j)) - p2, a);
-    a = fmaf(K.cz[2], (comp(Q[(C + 2) % 9], j) + comp(Q[(C + 7) % 9], j)) - p2, a);
-    a = fmaf(K.cz[1], (comp(Q[(C + 1) % 9], j) + comp(Q[(C + 8) % 9], j)) - p2, a);
-    lap[j] = a;
+  for (int j = 0; j < 4; j += 2) {
+    const float2 p = f2(w[4 + j], w[5 + j]);
+    const float2 p2 = __fadd2_rn(p, p);
+    auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+    auto ys = [&](int k) { return __fadd2_rn(half2of(yn[k + 3], j), half2of(yn[k - 1], j)); };
+    auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % 9], j), half2of(Q[(C + 9 - k) % 9], j)); };
+    float2 a = __fmul2_rn(f2(K.cx[4], K.cx[4]), __ffma2_rn(p2, m1, xs(4)));
+    a = __ffma2_rn(f2(K.cx[3], K.cx[3]), __ffma2_rn(p2, m1, xs(3)), a);
+    a = __ffma2_rn(f2(K.cx[2], K.cx[2]), __ffma2_rn(p2, m1, xs(2)), a);
+    a = __ffma2_rn(f2(K.cx[1], K.cx[1]), __ffma2_rn(p2, m1, xs(1)), a);
+    a = __ffma2_rn(f2(K.cy[4], K.cy[4]), __ffma2_rn(p2, m1, ys(4)), a);
+    a = __ffma2_rn(f2(K.cy[3], K.cy[3]), __ffma2_rn(p2, m1, ys(3)), a);
+    a = __ffma2_rn(f2(K.cy[2], K.cy[2]), __ffma2_rn(p2, m1, ys(2)), a);
+    a = __ffma2_rn(f2(K.cy[1], K.cy[1]), __ffma2_rn(p2, m1, ys(1)), a);
+    a = __ffma2_rn(f2(K.cz[4], K.cz[4]), __ffma2_rn(p2, m1, zs(4)), a);
+    a = __ffma2_rn(f2(K.cz[3], K.cz[3]), __ffma2_rn(p2, m1, zs(3)), a);
+    a = __ffma2_rn(f2(K.cz[2], K.cz[2]), __ffma2_rn(p2, m1, zs(2)), a);
+    a = __ffma2_rn(f2(K.cz[1], K.cz[1]), __ffma2_rn(p2, m1, zs(1)), a);
+    lap[j] = a.x;
+    lap[j + 1] = a.y;
   }
 }
 
@@ -155,10 +167,13 @@ struct March3D {
       const float gzy = gz[z] + gyv;
       float nv[4];
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const float bb = sponge_b(gzy + gxv[j]);
-        const float p = comp(Q[C % 9], j);
-        nv[j] = fmaf(comp(cv, j), lap[j], fmaf(bb, p - comp(pm, j), p));
+      for (int j = 0; j < 4; j += 2) {  // cc * lap + (p + b (p - pm)), in pairs
+        const float2 bb = f2(sponge_b(gzy + gxv[j]), sponge_b(gzy + gxv[j + 1]));
+        const float2 p = half2of(Q[C % 9], j);
+        const float2 d = __ffma2_rn(half2of(pm, j), f2(-1.f, -1.f), p);
+        const float2 n2 = __ffma2_rn(half2of(cv, j), f2(lap[j], lap[j + 1]), __ffma2_rn(bb, d, p));
+        nv[j] = n2.x;
+        nv[j + 1] = n2.y;
       }
       // injection / sampling at this level: staged in this warp's row of the
       // p^{n-1} plane (already consumed)
@@ -198,8 +213,9 @@ struct March3D {
         const float4 g = ld4s(stage + S::OFF_G + ly * TX + lx);
         if (colv) {
           float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
-          const float gv[4] = {fmaf(nv[0], lps[0], g.x), fmaf(nv[1], lps[1], g.y), fmaf(nv[2], lps[2], g.z),
-                               fmaf(nv[3], lps[3], g.w)};
+          const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
+          const float2 g23 = __ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w));
+          const float gv[4] = {g01.x, g01.y, g23.x, g23.y};
           if (gx + 3 < L.nxp) {
             *reinterpret_cast<float4*>(gp) = make_float4(gv[0], gv[1], gv[2], gv[3]);
           } else {
