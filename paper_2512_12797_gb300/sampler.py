@@ -100,6 +100,26 @@ class RMSPreconditioner:
         g.div_(vhat.sqrt().add_(self.eps))
 
 
+class AdamState:
+    """Adam moments (Kingma & Ba 2015) for the deterministic refinement variant
+    (A15): g -> m-hat / (sqrt(v-hat) + eps) in place, m and v the exponential
+    moving averages of g and g^2 (beta1 0.9, beta2 0.999)."""
+
+    def __init__(self, like, beta1=0.9, beta2=0.999, eps=1e-8):
+        import torch
+        self.m = torch.zeros_like(like)
+        self.v = torch.zeros_like(like)
+        self.b1, self.b2, self.eps, self.n = beta1, beta2, eps, 0
+
+    def __call__(self, g):
+        self.n += 1
+        self.m.mul_(self.b1).add_(g, alpha=1.0 - self.b1)
+        self.v.mul_(self.b2).addcmul_(g, g, value=1.0 - self.b2)
+        mhat = self.m / (1.0 - self.b1 ** self.n)
+        vhat = self.v / (1.0 - self.b2 ** self.n)
+        g.copy_(mhat / (vhat.sqrt() + self.eps))
+
+
 def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, prior_lam=0.0, prior_mu=0.0,
                    zref=None, seed=0, record_every=1, sg_sizes=None):
     """Unadjusted Langevin on the full-shot likelihood (+ smoothness prior).
@@ -149,8 +169,15 @@ def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, pri
 
 
 def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_start, stride, K, eta, nu, vmin, vmax,
-                              sigma, denoiser=None, seed=0, renoise_on=True):
+                              sigma, denoiser=None, seed=0, renoise_on=True, refine="langevin"):
     """Decoupled encoded-shot diffusion sampler (Sec. 2.3, Algorithm table).
+
+    refine: "langevin" -- K Langevin steps per guided level (Sec. 2.3 (ii));
+            "adam"     -- K deterministic Adam steps on the same encoded
+                          likelihood instead (the deterministic refinement of
+                          Sec. 3.2, A15), no injected noise.  The two differ only
+                          there, which is the stochastic-vs-deterministic
+                          refinement ablation (E10).
 
     v_init: [nz, nx] initial model (m/s).  Starts from level t_start with
     x_t = sqrt(abar) x_init + sqrt(1 - abar) eps; guided levels are every
@@ -170,7 +197,10 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
            math.sqrt(1 - abar[t - 1]) * torch.randn((nsamp,) + tuple(v_init.shape), device=dev, generator=gen))
     x_t = x_t.contiguous()
     grad = torch.empty_like(x_t)
-    precond = RMSPreconditioner(x_t)
+    if refine not in ("langevin", "adam"):
+        raise ValueError("refine must be 'langevin' or 'adam'")
+    precond = RMSPreconditioner(x_t) if refine == "langevin" else AdamState(x_t)
+    step_nu = nu if refine == "langevin" else 0.0
     hist_r, hist_s = [_rmse(v_init, truth)], [0]
     solves = 0
     it = 0
@@ -187,9 +217,10 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
                 perm = np.stack([e[0] for e in encs])
                 w = np.stack([e[1] for e in encs])
                 ctx.gradient(z, perm, w, sg_sizes, d_obs, sigma, grad=grad)
-                _rms_normalise(grad)
+                if refine == "langevin":
+                    _rms_normalise(grad)
                 precond(grad)
-                langevin_step(z, grad, eta, nu, vmin, vmax, seed + 1, it)
+                langevin_step(z, grad, eta, step_nu, vmin, vmax, seed + 1, it)
                 solves += 2 * nsg * nsamp
                 it += 1
             x0 = normalize(z, vmin, vmax).contiguous()
