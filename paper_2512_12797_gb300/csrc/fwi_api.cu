@@ -220,6 +220,7 @@ Coef make_coef(const fwi_grid* g) {
   const double gmax = g->nb > 0 ? 3.0 * g->sponge_vmax * log(1.0 / g->sponge_R) / (2.0 * g->nb * hmin) : 0.0;
   K.gdt = (float)(gmax * g->dt);
   K.inv_nb = g->nb > 0 ? (float)(1.0 / g->nb) : 0.f;
+  K.c0_2d = (float)(A8[0] / (g->hx * g->hx) + A8[0] / (g->hz * g->hz));
   return K;
 }
 

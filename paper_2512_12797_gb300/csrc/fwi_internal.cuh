@@ -41,6 +41,7 @@ struct Coef {
   float cz[5], cy[5], cx[5];  // a_k / h_a^2, k = 1..4 used (sum-zero form)
   float gdt;                  // gmax * dt
   float inv_nb;               // 1 / nb (0 when nb == 0)
+  float c0_2d;                // a_0/hx^2 + a_0/hz^2: centre weight of the 2D Laplacian in plain form
 };
 
 // Slots and record time of one step of a multi-step launch.

@@ -142,6 +142,48 @@ __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, i
   }
 }
 
+// The Laplacian of the snapshot for the imaging condition, in the plain form
+// c0 p + sum_k c_k [(x_{+k} + x_{-k}) (+ (z_{+k} + z_{-k}))]: it only enters
+// the gradient, not the recursion, so it does not need the bracket form's
+// exact zero on constant fields, and saves the 4 subtractions of 4p (or 2p)
+// per point.  Same pair arithmetic and operand loads as lap_block.
+template <int R, bool ISO>
+__device__ __forceinline__ void lap_img(const float* __restrict__ T, int r0, int c0, const Coef& K,
+                                        float (&lap)[R][4]) {
+  float4 zc[R + 8];
+#pragma unroll
+  for (int i = 0; i < R + 8; i++) zc[i] = lds4(T + (r0 + i) * HX + c0 + 4);
+  const float* zp = reinterpret_cast<const float*>(&zc[0]);
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const float4 xl = lds4(T + (r0 + r + 4) * HX + c0);
+    const float4 xr = lds4(T + (r0 + r + 4) * HX + c0 + 8);
+    const float4 ce = zc[r + 4];
+    const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
+#pragma unroll
+    for (int j = 0; j < 4; j += 2) {
+      const float2 p = f2(w[4 + j], w[5 + j]);
+      auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+      auto zs = [&](int k) {
+        return __fadd2_rn(f2(zp[4 * (r + 4 + k) + j], zp[4 * (r + 4 + k) + j + 1]),
+                          f2(zp[4 * (r + 4 - k) + j], zp[4 * (r + 4 - k) + j + 1]));
+      };
+      float2 a = __fmul2_rn(f2(K.c0_2d, K.c0_2d), p);
+      if (ISO) {
+#pragma unroll
+        for (int k = 4; k >= 1; k--) a = __ffma2_rn(f2(K.cx[k], K.cx[k]), __fadd2_rn(xs(k), zs(k)), a);
+      } else {
+#pragma unroll
+        for (int k = 4; k >= 1; k--) a = __ffma2_rn(f2(K.cx[k], K.cx[k]), xs(k), a);
+#pragma unroll
+        for (int k = 4; k >= 1; k--) a = __ffma2_rn(f2(K.cz[k], K.cz[k]), zs(k), a);
+      }
+      lap[r][j] = a.x;
+      lap[r][j + 1] = a.y;
+    }
+  }
+}
+
 // Bounded poll of the progress flags of the 3 x 3 tile neighbourhood of item
 // (s, tile) until each has completed `need` steps; then acquire-orders the
 // neighbours' stores before the TMA loads that follow.  Gives up on timeout,
@@ -615,8 +657,8 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
             fence_proxy_async_shared();
           }
           if (ADJ) {
-            float lps[R][4], dummy[R][4];
-            lap_block<R, ISO>(I + S::OFF_SNAP, lz, lx, K, lps, dummy);
+            float lps[R][4];
+            lap_img<R, ISO>(I + S::OFF_SNAP, lz, lx, K, lps);
 #pragma unroll
             for (int r = 0; r < R; r++)
 #pragma unroll
