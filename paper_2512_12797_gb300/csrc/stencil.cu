@@ -111,7 +111,11 @@ __device__ __forceinline__ void lap_block(const float* __restrict__ T, int r0, i
     for (int j = 0; j < 4; j += 2) {
       const float2 p = f2(w[4 + j], w[5 + j]);
       // (x_{+k} + x_{-k}) and (z_{+k} + z_{-k}) of the pair
-      auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+      // odd k straddles the float4 quads: two scalar adds whose results land in a pair
+      auto xs = [&](int k) {
+        return (k & 1) ? f2(w[4 + j + k] + w[4 + j - k], w[5 + j + k] + w[5 + j - k])
+                       : __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k]));
+      };
       auto zs = [&](int k) {
         return __fadd2_rn(f2(zp[4 * (r + 4 + k) + j], zp[4 * (r + 4 + k) + j + 1]),
                           f2(zp[4 * (r + 4 - k) + j], zp[4 * (r + 4 - k) + j + 1]));
@@ -163,7 +167,11 @@ __device__ __forceinline__ void lap_img(const float* __restrict__ T, int r0, int
 #pragma unroll
     for (int j = 0; j < 4; j += 2) {
       const float2 p = f2(w[4 + j], w[5 + j]);
-      auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+      // odd k straddles the float4 quads: two scalar adds whose results land in a pair
+      auto xs = [&](int k) {
+        return (k & 1) ? f2(w[4 + j + k] + w[4 + j - k], w[5 + j + k] + w[5 + j - k])
+                       : __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k]));
+      };
       auto zs = [&](int k) {
         return __fadd2_rn(f2(zp[4 * (r + 4 + k) + j], zp[4 * (r + 4 + k) + j + 1]),
                           f2(zp[4 * (r + 4 - k) + j], zp[4 * (r + 4 - k) + j + 1]));

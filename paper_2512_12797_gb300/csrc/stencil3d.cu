@@ -71,7 +71,11 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   for (int j = 0; j < 4; j += 2) {
     const float2 p = f2(w[4 + j], w[5 + j]);
     const float2 p2 = __fadd2_rn(p, p);
-    auto xs = [&](int k) { return __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k])); };
+    // odd k straddles the float4 quads: two scalar adds whose results land in a pair
+    auto xs = [&](int k) {
+      return (k & 1) ? f2(w[4 + j + k] + w[4 + j - k], w[5 + j + k] + w[5 + j - k])
+                     : __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k]));
+    };
     auto ys = [&](int k) { return __fadd2_rn(half2of(yn[k + 3], j), half2of(yn[k - 1], j)); };
     auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % 9], j), half2of(Q[(C + 9 - k) % 9], j)); };
     float2 a = __fmul2_rn(f2(K.cx[4], K.cx[4]), __ffma2_rn(p2, m1, xs(4)));
