@@ -16,8 +16,10 @@
 // the snapshot p^{k-1} with its own register queue for L p^{k-1}.  Level
 // z = q - 8 is computed once sequence q has landed.  Every warp releases the
 // slot of sequence q-4 after computing level q-8 (per-warp "empty" mbarrier
-// arrivals); lane 0 of the last warp refills slots as they free up, blocking
-// only for the sequence its own warp needs next.
+// arrivals).  The CTA is warp-specialised: warps 0-7 compute (one y row each),
+// and lane 0 of warp 8 (a producer warpgroup that setmaxnreg shrinks) refills
+// the ring in sequence order, waiting on each slot's "empty" barrier, so that
+// no consumer warp carries the refill work.
 #include "fwi_internal.cuh"
 
 namespace fwi {
@@ -25,6 +27,11 @@ namespace fwi {
 constexpr int HY3 = TY3 + 2 * HALO;  // 16
 constexpr int PLANE = HY3 * HX;      // floats in a halo plane
 constexpr int PPLANE = TY3 * TX;     // floats in a plain plane
+constexpr int NCW3 = TY3;                // consumer warps (one y row each)
+constexpr int NTHREADS3 = 32 * NCW3 + 128;  // + producer warpgroup
+constexpr int REG3_LAUNCH = 168, REG3_PRODUCER = 72, REG3_CONSUMER = 216;
+static_assert(128 * REG3_PRODUCER + 32 * NCW3 * REG3_CONSUMER <= NTHREADS3 * REG3_LAUNCH,
+              "register split exceeds the launch allocation");
 
 template <bool ADJ>
 struct Smem3D {
@@ -35,7 +42,7 @@ struct Smem3D {
   static constexpr int OFF_G = OFF_CC + PPLANE;
   static constexpr int STAGE = OFF_G + (ADJ ? PPLANE : 0);
   static constexpr int OFF_GZ = NST * STAGE;  // gamma*dt of every z level
-  static size_t bytes(int nzp) { return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + 2 * NST * 8; }
+  static size_t bytes(int nzp) { return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + 2 * NST * 8 + 16; }
 };
 
 __device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -109,8 +116,9 @@ struct March3D {
   float* sm;
   uint64_t* full;
   uint64_t* empty;
+  volatile int* abort_flag;
   int lane, ly, lx, x0, y0, gx, gy, b, s, tile, last_q;
-  bool colv, producer;
+  bool colv;
   float gyv, gxv[4];
   const float* gz;       // shared gamma*dt per z level
   int pq, pst;           // producer: next sequence, its slot
@@ -136,27 +144,12 @@ struct March3D {
     if (++pst == NST) { pst = 0; pround ^= 1; }
   }
 
-  // Issue every sequence whose slot all warps have released; block only for `need`.
-  __device__ __forceinline__ bool refill(int need) {
-    while (pq <= last_q && pq <= need + NST - 5) {
-      if (pq >= NST) {
-        if (pq <= need) {
-          if (!mbar_wait_bounded(&empty[pst], pround ^ 1, P.status)) return false;
-        } else if (!mbar_try_wait(&empty[pst], pround ^ 1)) {
-          break;
-        }
-      }
-      issue();
-    }
-    return true;
-  }
 
   // Sequence q with the queue centre at compile-time index C = (q - 4) % 9.
   template <int C>
   __device__ __forceinline__ bool step(int q) {
     const int slot = q % NST;
-    if (producer && !refill(q)) return false;
-    if (!mbar_wait_bounded(&full[slot], (uint32_t)((q / NST) & 1), P.status)) return false;
+    if (!mbar_wait_abortable(&full[slot], (uint32_t)((q / NST) & 1), P.status, abort_flag)) return false;
     float* stage = sm + slot * S::STAGE;
     // the centre of halo plane q-4 enters the queue at index (C + 4) % 9
     Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX + lx + HALO);
@@ -248,7 +241,7 @@ struct March3D {
 };
 
 template <bool ADJ>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS3, 1)
 step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_cc, const __grid_constant__ CUtensorMap tm_g, const Layout L,
               const Coef K, const StepParams P) {
@@ -258,11 +251,12 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   float* gz = sm + S::OFF_GZ;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)S::OFF_GZ + ((L.nzp + 31) / 32) * 32) * 4));
   uint64_t* empty = full + S::NST;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST);
 
-  const int tid = threadIdx.x;
-  March3D<ADJ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty};
+  const int tid = threadIdx.x, warp = tid >> 5;
+  March3D<ADJ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
   M.lane = tid & 31;
-  M.ly = tid >> 5;
+  M.ly = warp;
   M.x0 = blockIdx.x * TX;
   M.y0 = blockIdx.y * TY3;
   M.b = blockIdx.z;
@@ -273,7 +267,6 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.gy = M.y0 + M.ly;
   M.colv = M.gx < L.nxp && M.gy < L.nyp;
   M.last_q = L.nzp + 7;
-  M.producer = tid == NTHREADS - 32;
   M.gz = gz;
   M.pq = 0;
   M.pst = 0;
@@ -286,12 +279,36 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     if (ADJ) tma_prefetch_desc(&tm_g);
     for (int i = 0; i < S::NST; i++) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], NTHREADS / 32);
+      mbar_init(&empty[i], NCW3);
     }
+    *abort_flag = 0;
     fence_mbar_init();
   }
-  for (int i = tid; i < L.nzp; i += NTHREADS) gz[i] = P.gtab[i];
+  for (int i = tid; i < L.nzp; i += NTHREADS3) gz[i] = P.gtab[i];
   __syncthreads();
+
+  if (warp >= NCW3) {  // -------------------------------------------- producer warpgroup
+    setmaxnreg_dec<REG3_PRODUCER>();
+    if (warp == NCW3 && M.lane == 0) {
+      // sequence q into slot q % NST once every consumer warp has released
+      // sequence q - NST (whose halo plane served level q - NST - 4)
+      while (M.pq <= M.last_q) {
+        if (M.pq >= S::NST &&
+            !mbar_wait_abortable(&empty[M.pst], (uint32_t)((M.pq / S::NST - 1) & 1), P.status, abort_flag))
+          break;
+        M.issue();
+      }
+      if (M.pq <= M.last_q) {  // gave up: bounded wait for the copies in flight
+        for (int i = M.pq - S::NST > 0 ? M.pq - S::NST : 0; i < M.pq; i++) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[i % S::NST], (uint32_t)((i / S::NST) & 1)) && clock64() - t0 < (1LL << 24)) {
+          }
+        }
+      }
+    }
+    return;
+  }
+  setmaxnreg_inc<REG3_CONSUMER>();
 
   M.gyv = M.gy < L.nyp ? __ldg(P.gtab + L.nzp + M.gy) : 0.f;
 #pragma unroll
@@ -307,9 +324,6 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     M.Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     M.QS[i] = M.Q[i];
   }
-  if (M.producer)
-    while (M.pq <= M.last_q && M.pq < S::NST - 4) M.issue();
-
   // sequence q has queue centre index (q - 4) mod 9 = (q + 5) mod 9
   int q = 0;
   for (; q + 9 <= M.last_q + 1; q += 9) {
@@ -343,12 +357,12 @@ cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMa
     const size_t bytes = Smem3D<true>::bytes(L.nzp);
     cudaError_t e = cudaFuncSetAttribute(step3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    step3d_kernel<true><<<grid, NTHREADS, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
+    step3d_kernel<true><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
   } else {
     const size_t bytes = Smem3D<false>::bytes(L.nzp);
     cudaError_t e = cudaFuncSetAttribute(step3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    step3d_kernel<false><<<grid, NTHREADS, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
+    step3d_kernel<false><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
   }
   return cudaGetLastError();
 }
