@@ -271,18 +271,42 @@ def native_arm(args):
     dobs_h = torch.tensor(d_obs_h).pin_memory()
     out_h = torch.empty_like(vel_h).pin_memory()
     mis_h = torch.empty(nsamp, dtype=torch.float64).pin_memory()
-    vel_e = torch.empty_like(vel)
-    dobs_e = torch.empty_like(d_obs)
+    # Double-buffered: step k+1's inputs are copied on a copy stream while step
+    # k computes (they do not depend on its results); every step still copies
+    # its own inputs and reads back its own result inside the timed region.
+    vel_e = [torch.empty_like(vel) for _ in range(2)]
+    dobs_e = [torch.empty_like(d_obs) for _ in range(2)]
+    cstream = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    e2e_range = {}
+
+    def prefetch(it):
+        b = it % 2
+        cstream.wait_event(free[b])  # the step that used buffer b is done with it
+        with torch.cuda.stream(cstream):
+            vel_e[b].copy_(vel_h, non_blocking=True)
+            dobs_e[b].copy_(dobs_h, non_blocking=True)
+        ready[b].record(cstream)
 
     def step_e2e(it):
-        vel_e.copy_(vel_h, non_blocking=True)
-        dobs_e.copy_(dobs_h, non_blocking=True)
-        step(it, vel_e, dobs_e)
-        out_h.copy_(vel_e, non_blocking=True)
+        b = it % 2
+        if it == e2e_range["first"]:
+            prefetch(it)
+        torch.cuda.current_stream().wait_event(ready[b])
+        if it + 1 < e2e_range["end"]:
+            prefetch(it + 1)
+        step(it, vel_e[b], dobs_e[b])
+        out_h.copy_(vel_e[b], non_blocking=True)
         mis_h.copy_(misfit, non_blocking=True)
+        free[b].record()
 
+    e2e_range.update(first=0, end=1)
     step_e2e(0)
-    ms_e2e, _ = timed(step_e2e, max(1, args.steps), 2000)
+    torch.cuda.synchronize()
+    n_e2e = max(1, args.steps)
+    e2e_range.update(first=2000, end=2000 + n_e2e)
+    ms_e2e, _ = timed(step_e2e, n_e2e, 2000)
     e2e_value = job_throughput(units, world, ms_e2e) / 1e9
     h2d = vel_h.numel() * 4 + dobs_h.numel() * 4
     d2h = out_h.numel() * 4 + nsamp * 8
@@ -335,7 +359,8 @@ def native_arm(args):
                                        "tuner_ms_forward": variants["forward_ms"],
                                        "tuner_ms_adjoint": variants["adjoint_ms"]}},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "ms_per_step": ms_e2e},
+                   "ms_per_step": ms_e2e,
+                   "overlap": "double-buffered inputs: step k+1's H2D on a copy stream during step k"},
            "gpu_launches": int(phase_launch.sum() + n * 2),
            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak,
