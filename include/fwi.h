@@ -143,6 +143,22 @@ int fwi_gradient(fwi_ctx* ctx, const float* vel, int nsamp, const int32_t* perm,
                  double sigma_y, double scale, float* grad, double* misfit, void* stream);
 
 /*
+ * Transposed Jacobian of the encoded records (the adjoint-state method of
+ * Sec. 2.1 with an arbitrary adjoint source): for each sample s,
+ *   grad[s] = sum_j (dF~_j(v_s)/dv_s)^T d_cot[s][j]
+ * where F~_j is the record fwi_forward returns for supergather j.  It is
+ * fwi_gradient with the cotangent in place of the scaled residual
+ * (d~_j - F~_j)/sigma_y^2 and with scale 1: same forward solve with
+ * checkpointing, same adjoint solve and imaging, no misfit.  This is the
+ * backward of the records as a differentiable function of velocity.
+ *   d_cot    device [nsamp][nsg][nt][nr]  cotangent of the records (read only)
+ *   grad     device [nsamp][phys]         OVERWRITTEN
+ * Other arguments and errors as fwi_forward.
+ */
+int fwi_adjoint(fwi_ctx* ctx, const float* vel, int nsamp, const int32_t* perm, const int8_t* w,
+                const int32_t* sg_sizes, int nsg, const float* d_cot, float* grad, void* stream);
+
+/*
  * Clean-space Langevin refinement step (Sec. 2.3 (ii), with the independent
  * noise scale of the modified refinement step, Sec. 2.3 closing paragraph):
  *   z <- clamp(z - eta * grad + nu * xi, vmin, vmax)

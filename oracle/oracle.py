@@ -320,6 +320,24 @@ def gradient(g, v, src, rec, d_obs, perm, w, sg_sizes, sigma, scale=None):
     return scale * phi, scale * fold_gradient(g, v, gc)
 
 
+def records_vjp(g, v, src, rec, perm, w, sg_sizes, d_cot):
+    """Transposed Jacobian of the encoded records applied to a record
+    cotangent, for one sample (the adjoint-state method of Sec. 2.1 with an
+    arbitrary adjoint source):  grad[phys] = sum_j (dF~_j/dv)^T d_cot[j].
+    """
+    vpad = pad_velocity(g, v)
+    rec_idx = pad_index(g, rec)
+    gc = np.zeros(g.npad)
+    for j, B in enumerate(supergathers(perm, sg_sizes)):
+        src_idx = pad_index(g, src[B])
+        ts = source_series(g, w[B].astype(np.float64))
+        _, snaps = forward_raw(g, vpad, src_idx, ts, rec_idx, keep_snaps=True)
+        gcj, _ = adjoint_raw(g, vpad, snaps, src_idx, ts, rec_idx, d_cot[j])
+        gc += gcj
+        del snaps
+    return fold_gradient(g, v, gc)
+
+
 def full_misfit(g, v, src, rec, d_obs, sigma):
     """Full-shot misfit Phi(x) = 1/(2 sigma^2) sum_i ||d_i - F_i(x)||^2 (Sec. 2.1)."""
     phi = 0.0

@@ -113,6 +113,22 @@ class FWI:
                                  _stream(stream)), "fwi_gradient")
         return misfit, grad
 
+    def adjoint(self, vel, perm, w, sg_sizes, d_cot, grad=None, stream=None):
+        """Transposed Jacobian of the encoded records applied to d_cot
+        [nsamp][nsg][nt][nr]: grad [nsamp, *shape] float32 (fwi_adjoint)."""
+        torch = _torch()
+        nsamp = vel.shape[0]
+        keep = self._enc(nsamp, perm, w, sg_sizes)
+        nsg = len(keep[2])
+        if tuple(d_cot.shape) != (nsamp, nsg, self.nt, self.nr):
+            raise ValueError("d_cot must have shape %s, got %s" % ((nsamp, nsg, self.nt, self.nr), tuple(d_cot.shape)))
+        if grad is None:
+            grad = torch.empty_like(vel)
+        check(lib().fwi_adjoint(self._h, _dev_ptr(vel, torch.float32, "vel"), nsamp, keep[3], keep[4], keep[5], nsg,
+                                _dev_ptr(d_cot, torch.float32, "d_cot"), _dev_ptr(grad, torch.float32, "grad"),
+                                _stream(stream)), "fwi_adjoint")
+        return grad
+
     def smooth_prior_grad(self, z, zref, lam, mu, grad, stream=None):
         """grad += gradient of the Gaussian smoothness prior (smooth_prior_grad)."""
         torch = _torch()

@@ -905,9 +905,12 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
 // One chunk of samples through forward, residual/misfit, reverse sweep and
 // fold.  The pool is partitioned for Bpart >= nsamp*nsg wavefields, so every
 // chunk of a call (the last one may be smaller) shares one slot layout.
+// With cot != nullptr the chunk applies the transposed Jacobian of the
+// records instead: cot (this chunk's [B][nt][nr] cotangent) takes the place
+// of the residual and no misfit is formed.
 static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w,
-                          const int32_t* sg, int nsg, const float* d_obs, double sigma_y, double scale, float* grad,
-                          double* misfit, cudaStream_t st, int Bpart) {
+                          const int32_t* sg, int nsg, const float* d_obs, const float* cot, double sigma_y,
+                          double scale, float* grad, double* misfit, cudaStream_t st, int Bpart) {
   int rc;
   const int B = nsamp * nsg;
   const int nt = C->g.nt, nr = C->nr;
@@ -951,13 +954,17 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
-  // residual (rhat overwrites dpred) and misfit
-  const double inv_s2 = 1.0 / (sigma_y * sigma_y);
-  CK(launch_residual(B, nt, nr, C->dpred, d_obs, reinterpret_cast<const int*>(C->dlist + cl.shot_off),
-                     reinterpret_cast<const int*>(C->dlist + cl.shot_id),
-                     reinterpret_cast<const float*>(C->dlist + cl.shot_w), inv_s2, C->dpred, C->part, C->nblk, st));
-  CK(launch_misfit(nsamp, nsg, C->part, C->nblk, scale * 0.5 * inv_s2, misfit, C->status, st));
-  C->launches[1] += 2;
+  if (cot) {  // the given cotangent is the adjoint source
+    CK(cudaMemcpyAsync(C->dpred, cot, (size_t)B * nt * nr * 4, cudaMemcpyDeviceToDevice, st));
+  } else {  // residual (rhat overwrites dpred) and misfit
+    const double inv_s2 = 1.0 / (sigma_y * sigma_y);
+    CK(launch_residual(B, nt, nr, C->dpred, d_obs, reinterpret_cast<const int*>(C->dlist + cl.shot_off),
+                       reinterpret_cast<const int*>(C->dlist + cl.shot_id),
+                       reinterpret_cast<const float*>(C->dlist + cl.shot_w), inv_s2, C->dpred, C->part, C->nblk,
+                       st));
+    CK(launch_misfit(nsamp, nsg, C->part, C->nblk, scale * 0.5 * inv_s2, misfit, C->status, st));
+    C->launches[1] += 2;
+  }
   prof_mark(C, 2, st);
 
   // reverse sweep: recompute each earlier segment, then the adjoint steps
@@ -1011,19 +1018,12 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   return FWI_OK;
 }
 
-int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
-                 int nsg, const float* d_obs, double sigma_y, double scale, float* grad, double* misfit,
-                 void* stream) {
-  int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
-  if (rc != FWI_OK) return rc;
-  if (!d_obs || !grad || !misfit || !(sigma_y > 0)) return FWI_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+// Shared driver of fwi_gradient (d_obs set) and fwi_adjoint (cot set):
+// chunking of the samples, then one gradient_chunk per chunk.
+static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w,
+                          const int32_t* sg, int nsg, const float* d_obs, const float* cot, double sigma_y,
+                          double scale, float* grad, double* misfit, cudaStream_t st) {
   const int nt = C->g.nt;
-  if (!(scale > 0)) {
-    long long tot = 0;
-    for (int j = 0; j < nsg; j++) tot += sg[j];
-    scale = (double)C->ns / (double)tot;
-  }
   // Samples per chunk: the whole batch when its checkpoint plan fits the pool,
   // otherwise the chunk size that minimises (chunks) x (2 nt + recomputed
   // steps) x (time of one step).  In 2D all steps of a phase share one launch
@@ -1067,11 +1067,37 @@ int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, c
   const long long phys = C->L.phys;
   for (int s0 = 0; s0 < nsamp; s0 += best_c) {
     const int n = std::min(best_c, nsamp - s0);
-    rc = gradient_chunk(C, vel + (size_t)s0 * phys, n, perm + (size_t)s0 * C->ns, w + (size_t)s0 * C->ns, sg, nsg,
-                        d_obs, sigma_y, scale, grad + (size_t)s0 * phys, misfit + s0, st, best_c * nsg);
+    const size_t rec0 = (size_t)s0 * nsg * nt * C->nr;
+    const int rc = gradient_chunk(C, vel + (size_t)s0 * phys, n, perm + (size_t)s0 * C->ns, w + (size_t)s0 * C->ns,
+                                  sg, nsg, d_obs, cot ? cot + rec0 : nullptr, sigma_y, scale,
+                                  grad + (size_t)s0 * phys, misfit ? misfit + s0 : nullptr, st, best_c * nsg);
     if (rc != FWI_OK) return rc;
   }
   return FWI_OK;
+}
+
+int fwi_gradient(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                 int nsg, const float* d_obs, double sigma_y, double scale, float* grad, double* misfit,
+                 void* stream) {
+  const int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
+  if (rc != FWI_OK) return rc;
+  if (!d_obs || !grad || !misfit || !(sigma_y > 0)) return FWI_ERR_ARG;
+  if (!(scale > 0)) {
+    long long tot = 0;
+    for (int j = 0; j < nsg; j++) tot += sg[j];
+    scale = (double)C->ns / (double)tot;
+  }
+  return gradient_calls(C, vel, nsamp, perm, w, sg, nsg, d_obs, nullptr, sigma_y, scale, grad, misfit,
+                        (cudaStream_t)stream);
+}
+
+int fwi_adjoint(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
+                int nsg, const float* d_cot, float* grad, void* stream) {
+  const int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
+  if (rc != FWI_OK) return rc;
+  if (!d_cot || !grad) return FWI_ERR_ARG;
+  return gradient_calls(C, vel, nsamp, perm, w, sg, nsg, nullptr, d_cot, 1.0, 1.0, grad, nullptr,
+                        (cudaStream_t)stream);
 }
 
 int langevin_step(float* z, const float* grad, int64_t n, double eta, double nu, double vmin, double vmax,

@@ -286,6 +286,46 @@ def test_gradient_matches_central_differences(ndim):
     assert err1 / err2 > 3.0  # O(eps^2) convergence of the central difference
 
 
+def test_records_vjp_matches_central_differences():
+    # <dF~/dv dv, dd> from central differences of the encoded records alone
+    # equals <dv, records_vjp(dd)>, with O(eps^2) convergence; two uneven
+    # supergathers, so the sum over supergathers is exercised.
+    w_ = synth.tiny2d(nt=120, ns=4)
+    g = O.Grid.from_workload(w_)
+    v = synth.models.random_smooth_model(w_.shape, 3, 1500, 2500).astype(np.float64)
+    perm, w = O.encode(4, 2, w_.ns)
+    sg = [3, 1]
+    rng = np.random.default_rng(8)
+    dd = rng.normal(0, 1, (len(sg), g.nt, len(w_.rec)))
+    dv = rng.normal(0, 1, v.shape)
+    dirn = float(np.sum(O.records_vjp(g, v, w_.src, w_.rec, perm, w, sg, dd) * dv))
+
+    def F(x):
+        return O.encoded_forward(g, x, w_.src, w_.rec, perm, w, sg)
+
+    errs = []
+    for e in (1.0, 0.5):
+        fd = float(np.sum((F(v + e * dv) - F(v - e * dv)) * dd)) / (2 * e)
+        errs.append(abs(fd - dirn))
+    assert errs[1] < 1e-4 * abs(dirn)
+    assert errs[0] / errs[1] > 3.0
+
+
+def test_gradient_is_records_vjp_of_scaled_residual():
+    # Sec. 2.1: the misfit gradient is the transposed Jacobian applied to
+    # (F~_j - d~_j)/sigma^2, times the supergather scaling.
+    w_ = synth.tiny2d(nt=100, ns=4)
+    g = O.Grid.from_workload(w_)
+    v = synth.models.random_smooth_model(w_.shape, 6, 1500, 2500)
+    d_obs = synth.random_records(w_, 3)
+    perm, w = O.encode(2, 5, w_.ns)
+    sg, sig, scale = [2, 1], 0.7, 1.3
+    _, grad = O.gradient(g, v, w_.src, w_.rec, d_obs, perm, w, sg, sig, scale)
+    r = O.encoded_forward(g, v, w_.src, w_.rec, perm, w, sg) - O.encoded_data(d_obs, perm, w, sg)
+    vjp = O.records_vjp(g, v, w_.src, w_.rec, perm, w, sg, r / sig ** 2)
+    assert _rel(grad, scale * vjp) < 1e-12
+
+
 def test_encoded_estimator_unbiased_exactly():
     # Sec. 2.1: E_w[Phi~] = Phi and E_w[grad Phi~] = grad Phi for zero-mean,
     # unit-variance weights: averaging over all 2^M sign patterns cancels the
