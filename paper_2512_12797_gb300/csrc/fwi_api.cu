@@ -225,14 +225,13 @@ Coef make_coef(const fwi_grid* g) {
 }
 
 // Tile of padded point (z, y, x) and its local index inside the tile.
-// 2D tiles are 128 (x) x 32 (z); 3D tiles are 128 (x) x 8 (y) columns in z.
+// 2D tiles are 128 (x) x 32 (z); 3D tiles are 64 (x) x 16 (y) columns in z.
 void tile_of(const fwi_ctx* C, const Entry& e, int* tile, int* local) {
-  const int tx = e.x / TX;
   if (C->L.ndim == 3) {
-    *tile = (e.y / TY3) * C->ntx + tx;
-    *local = (e.y % TY3) * TX + (e.x % TX);
+    *tile = (e.y / TY3) * C->ntx + e.x / TX3;
+    *local = (e.y % TY3) * TX3 + (e.x % TX3);
   } else {
-    *tile = (e.z / TZ) * C->ntx + tx;
+    *tile = (e.z / TZ) * C->ntx + e.x / TX;
     *local = (e.z % TZ) * TX + (e.x % TX);
   }
 }
@@ -297,7 +296,7 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
                               (cuuint64_t)nslots};
   const cuuint64_t str[4] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4,
                              (cuuint64_t)L.field * B * 4};
-  const cuuint32_t bh[5] = {HX, TY3 + 2 * HALO, 1, 1, 1}, bp[5] = {TX, TY3, 1, 1, 1};
+  const cuuint32_t bh[5] = {HX3, TY3 + 2 * HALO, 1, 1, 1}, bp[5] = {TX3, TY3, 1, 1, 1};
   if (enc(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, C->pool, dims, str, bh, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -309,7 +308,7 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* pl
   // cc per sample and the imaging accumulator per wavefield, plain planes
   const cuuint64_t d4[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
   const cuuint64_t s4[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4};
-  const cuuint32_t b4[4] = {TX, TY3, 1, 1};
+  const cuuint32_t b4[4] = {TX3, TY3, 1, 1};
   if (enc(ctile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->c, d4, s4, b4, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -677,7 +676,7 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
         delete C;
         return FWI_ERR_ARG;
       }
-  C->ntx = (L.nxp + TX - 1) / TX;
+  C->ntx = g->ndim == 3 ? (L.nxp + TX3 - 1) / TX3 : (L.nxp + TX - 1) / TX;
   C->ntz = (L.nzp + TZ - 1) / TZ;
   C->nty = (L.nyp + TY3 - 1) / TY3;
   C->ntiles = C->ntx * (g->ndim == 3 ? C->nty : C->ntz);
@@ -1031,8 +1030,9 @@ static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   // nsg supergathers (~1.7 us per tile), but at least ~15 us: with about one
   // item per CTA each step waits for its neighbours' previous one (flag,
   // fence, poll, TMA latency); plus ~20 us per launch (three per checkpoint
-  // segment).  In 3D every step is a launch of at least ~8 us.
-  const double pts = (double)C->L.nzp * C->L.nyp * C->L.nxp;
+  // segment).  In 3D every step is a launch of at least ~8 us that runs
+  // ceil(CTAs / SMs) waves of equal CTAs (one CTA per SM), each CTA a column
+  // of TX3 x TY3 x nzp points at ~16 B per point from a ~6 TB/s share.
   int nsm = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm <= 0) nsm = 1;
@@ -1049,7 +1049,9 @@ static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t
       cost = nchunks * ((2.0 * nt + (double)p.recompute) * std::max(per_cta * 1.7e-6, 15e-6) +
                         (1.0 + 2.0 * (p.jL + 1)) * 20e-6);
     } else {
-      const double t_launch = std::max(8e-6, c * nsg * pts * 16.0 / 6e12);
+      const double waves = std::ceil((double)c * nsg * C->ntiles / nsm);
+      const double t_wave = (double)TX3 * TY3 * C->L.nzp * 16.0 / (6e12 / nsm);
+      const double t_launch = std::max(8e-6, waves * t_wave);
       cost = nchunks * (2.0 * nt + (double)p.recompute) * t_launch;
     }
     if (best_c < 0 || cost < best_cost * 0.999) {

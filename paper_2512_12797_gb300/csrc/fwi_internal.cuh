@@ -22,7 +22,9 @@ constexpr int RZ = 4;     // rows per thread
 constexpr int NTHREADS = 256;
 constexpr int HX = TX + 2 * HALO;   // 136
 constexpr int HZ = TZ + 2 * HALO;   // 40
-constexpr int TY3 = 8;              // 3D tile height (y): 8 warps x 1 row
+constexpr int TX3 = 64;             // 3D tile width (x): 16 lanes x float4
+constexpr int TY3 = 16;             // 3D tile height (y): 8 warps x 2 rows
+constexpr int HX3 = TX3 + 2 * HALO; // 72
 
 struct Layout {
   int ndim;
@@ -66,7 +68,7 @@ struct StepParams {
   int ntx, ntiles;
   // injection points per (wavefield, tile): CSR offsets inj_off[b * inj_bstride + tile]
   const int* inj_off; int inj_bstride;
-  const int4* inj;          // {local = lz*TX + lx, col, amp (float bits), unused}
+  const int4* inj;          // {local = row * tile width + column, col, amp (float bits), unused}
   const float* series; long long series_bstride; int series_ld;  // amp * series[b*bs + t*ld + col]
   // sampling points, same CSR form; smp == nullptr disables sampling
   const int* smp_off; int smp_bstride;

@@ -5,18 +5,21 @@
 // (cc = v^2 dt^2/(1 + gamma dt) comes from the expanded array, b = (1 - gamma dt)/(1 + gamma dt)
 // from the per-axis gamma*dt table).
 //
-// 2.5D blocking: a CTA owns a 128 (x) x 8 (y) column of one wavefield and
-// marches through z; each thread owns 4 consecutive x points of one y row and
-// keeps the 9 z-levels its z-derivative needs in a circular register queue
-// (the level loop is unrolled by 9 so the queue never moves).  Ring
-// sequence q carries the x-y halo plane (136 x 16) of level q-4 -- whose
+// 2.5D blocking: a CTA owns a 64 (x) x 16 (y) column of one wavefield and
+// marches through z; each thread owns 4 consecutive x points of one y row (a
+// warp covers two rows, one per half-warp) and keeps the 9 z-levels its
+// z-derivative needs in a circular register queue (the level loop is unrolled
+// by 9 so the queue never moves).  64 x 16 rather than 128 x 8: the padded x
+// extents of the 3D grids (e.g. 296) leave less of a last x-tile idle, and the
+// halo plane is 1.7 rather than 2.1 times the tile.  Ring
+// sequence q carries the x-y halo plane (72 x 24) of level q-4 -- whose
 // centre enters the queue at q and whose x-y neighbours serve level q-4 at
-// q+4 -- and the plain planes (128 x 8) of level q-8: p^{n-1}, cc and, in the
+// q+4 -- and the plain planes (64 x 16) of level q-8: p^{n-1}, cc and, in the
 // adjoint, the imaging accumulator; the adjoint also streams halo planes of
 // the snapshot p^{k-1} with its own register queue for L p^{k-1}.  Level
 // z = q - 8 is computed once sequence q has landed.  Every warp releases the
 // slot of sequence q-4 after computing level q-8 (per-warp "empty" mbarrier
-// arrivals).  The CTA is warp-specialised: warps 0-7 compute (one y row each),
+// arrivals).  The CTA is warp-specialised: warps 0-7 compute (two y rows each),
 // and lane 0 of warp 8 (a producer warpgroup that setmaxnreg shrinks) refills
 // the ring in sequence order, waiting on each slot's "empty" barrier, so that
 // no consumer warp carries the refill work.
@@ -24,10 +27,10 @@
 
 namespace fwi {
 
-constexpr int HY3 = TY3 + 2 * HALO;  // 16
-constexpr int PLANE = HY3 * HX;      // floats in a halo plane
-constexpr int PPLANE = TY3 * TX;     // floats in a plain plane
-constexpr int NCW3 = TY3;                // consumer warps (one y row each)
+constexpr int HY3 = TY3 + 2 * HALO;  // 24
+constexpr int PLANE = HY3 * HX3;     // floats in a halo plane
+constexpr int PPLANE = TY3 * TX3;    // floats in a plain plane
+constexpr int NCW3 = TY3 / 2;        // consumer warps (two y rows each)
 constexpr int NTHREADS3 = 32 * NCW3 + 128;  // + producer warpgroup
 constexpr int REG3_LAUNCH = 168, REG3_PRODUCER = 72, REG3_CONSUMER = 216;
 static_assert(128 * REG3_PRODUCER + 32 * NCW3 * REG3_CONSUMER <= NTHREADS3 * REG3_LAUNCH,
@@ -35,7 +38,7 @@ static_assert(128 * REG3_PRODUCER + 32 * NCW3 * REG3_CONSUMER <= NTHREADS3 * REG
 
 template <bool ADJ>
 struct Smem3D {
-  static constexpr int NST = ADJ ? 7 : 10;  // ring slots
+  static constexpr int NST = ADJ ? 8 : 10;  // ring slots
   static constexpr int OFF_SNAP = PLANE;
   static constexpr int OFF_PREV = PLANE * (ADJ ? 2 : 1);
   static constexpr int OFF_CC = OFF_PREV + PPLANE;
@@ -55,7 +58,7 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 0 ? f2(v.x, v.y) : f2(v.z, v.w); }
 
 // Laplacian of the thread's 4 points: x and y neighbours from the halo plane H
-// (row ly+4, columns lx..lx+11), z neighbours from the circular register queue
+// (row ly+4, columns lx..lx+11, row stride HX3), z neighbours from the circular register queue
 // Q (Q[(C+k) % 9] holds level z+k, k = -4..4, C the index of the centre).
 // Adjacent columns are computed as pairs with the packed FP32 instructions;
 // each point sees the operations of the scalar form in the same order
@@ -63,15 +66,15 @@ __device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 
 template <int C>
 __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[9], int ly, int lx,
                                      const Coef& K, float (&lap)[4]) {
-  const float* row = H + (ly + HALO) * HX;
+  const float* row = H + (ly + HALO) * HX3;
   const float4 xl = ld4s(row + lx), xr = ld4s(row + lx + 8);
   const float4 ce = Q[C % 9];
   const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
   float4 yn[8];
 #pragma unroll
   for (int k = 1; k <= 4; k++) {
-    yn[k - 1] = ld4s(H + (ly + HALO - k) * HX + lx + 4);
-    yn[k + 3] = ld4s(H + (ly + HALO + k) * HX + lx + 4);
+    yn[k - 1] = ld4s(H + (ly + HALO - k) * HX3 + lx + 4);
+    yn[k + 3] = ld4s(H + (ly + HALO + k) * HX3 + lx + 4);
   }
   const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
@@ -152,15 +155,15 @@ struct March3D {
     if (!mbar_wait_abortable(&full[slot], (uint32_t)((q / NST) & 1), P.status, abort_flag)) return false;
     float* stage = sm + slot * S::STAGE;
     // the centre of halo plane q-4 enters the queue at index (C + 4) % 9
-    Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX + lx + HALO);
-    if (ADJ) QS[(C + 4) % 9] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX + lx + HALO);
+    Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX3 + lx + HALO);
+    if (ADJ) QS[(C + 4) % 9] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX3 + lx + HALO);
     const int z = q - 2 * HALO;
     if (z >= 0) {
       const float* hpl = sm + ((q - HALO) % NST) * S::STAGE;  // halo plane of level z
       float lap[4];
       lap3<C>(hpl, Q, ly, lx, K, lap);
-      const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX + lx);
-      const float4 cv = ld4s(stage + S::OFF_CC + ly * TX + lx);
+      const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX3 + lx);
+      const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
       const float gzy = gz[z] + gyv;
       float nv[4];
 #pragma unroll
@@ -172,33 +175,35 @@ struct March3D {
         nv[j] = n2.x;
         nv[j + 1] = n2.y;
       }
-      // injection / sampling at this level: staged in this warp's row of the
-      // p^{n-1} plane (already consumed)
+      // injection / sampling at this level: staged in this warp's two rows of
+      // the p^{n-1} plane (already consumed); entry .x is the point's index
+      // in that plane, and its row / 2 names the warp that owns it
       if (inj_z == z || smp_z == z) {
-        float* row = stage + S::OFF_PREV + ly * TX;
+        float* pl = stage + S::OFF_PREV;
+        const int wrow = ly >> 1;
         __syncwarp();
-        *reinterpret_cast<float4*>(row + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        *reinterpret_cast<float4*>(pl + ly * TX3 + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
         __syncwarp();
         int e_end = ie_cur;
         while (e_end < ie_end && P.inj[e_end].w == z) e_end++;
         for (int e = ie_cur + lane; e < e_end; e += 32) {
           const int4 en = P.inj[e];
-          if (en.x / TX != ly) continue;
-          const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + ly, x0 + en.x % TX));
-          row[en.x % TX] += ccp * (__int_as_float(en.z) *
-                                   P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
+          if ((en.x / TX3) >> 1 != wrow) continue;
+          const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + en.x / TX3, x0 + en.x % TX3));
+          pl[en.x] += ccp * (__int_as_float(en.z) *
+                             P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
         }
         ie_cur = e_end;
         inj_z = ie_cur < ie_end ? P.inj[ie_cur].w : 0x7fffffff;
         __syncwarp();
-        const float4 v = ld4s(row + lx);
+        const float4 v = ld4s(pl + ly * TX3 + lx);
         nv[0] = v.x; nv[1] = v.y; nv[2] = v.z; nv[3] = v.w;
         int s_end = se_cur;
         while (s_end < se_end && P.smp4[s_end].z == z) s_end++;
         for (int e = se_cur + lane; e < s_end; e += 32) {
           const int4 en = P.smp4[e];
-          if (en.x / TX != ly) continue;
-          P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = row[en.x % TX];
+          if ((en.x / TX3) >> 1 != wrow) continue;
+          P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = pl[en.x];
         }
         se_cur = s_end;
         smp_z = se_cur < se_end ? P.smp4[se_cur].z : 0x7fffffff;
@@ -207,7 +212,7 @@ struct March3D {
       if (ADJ) {
         float lps[4];
         lap3<C>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
-        const float4 g = ld4s(stage + S::OFF_G + ly * TX + lx);
+        const float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (colv) {
           float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
           const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
@@ -256,13 +261,13 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   const int tid = threadIdx.x, warp = tid >> 5;
   March3D<ADJ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
   M.lane = tid & 31;
-  M.ly = warp;
-  M.x0 = blockIdx.x * TX;
+  M.ly = 2 * warp + (tid >> 4 & 1);
+  M.x0 = blockIdx.x * TX3;
   M.y0 = blockIdx.y * TY3;
   M.b = blockIdx.z;
   M.s = M.b / P.nsg;
   M.tile = blockIdx.y * P.ntx + blockIdx.x;
-  M.lx = 4 * M.lane;
+  M.lx = 4 * (M.lane & 15);
   M.gx = M.x0 + M.lx;
   M.gy = M.y0 + M.ly;
   M.colv = M.gx < L.nxp && M.gy < L.nyp;
