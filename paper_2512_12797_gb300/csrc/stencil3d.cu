@@ -62,8 +62,12 @@ __device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 
 // Q (Q[(C+k) % 9] holds level z+k, k = -4..4, C the index of the centre).
 // Adjacent columns are computed as pairs with the packed FP32 instructions;
 // each point sees the operations of the scalar form in the same order
-// (x - y as fma(y, -1, x), exact).
-template <int C>
+// (x - y as fma(y, -1, x), exact).  ISO (hx == hy == hz): the axes share
+// coefficients and each k costs one bracket
+//   [(x_{+k} + x_{-k}) + (y_{+k} + y_{-k}) - 4p] + [(z_{+k} + z_{-k}) - 2p],
+// which is still exactly zero on a constant field, so the chain of
+// coefficient FMAs is 4 long instead of 12.
+template <int C, bool ISO>
 __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[9], int ly, int lx,
                                      const Coef& K, float (&lap)[4]) {
   const float* row = H + (ly + HALO) * HX3;
@@ -88,6 +92,19 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
     };
     auto ys = [&](int k) { return __fadd2_rn(half2of(yn[k + 3], j), half2of(yn[k - 1], j)); };
     auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % 9], j), half2of(Q[(C + 9 - k) % 9], j)); };
+    if (ISO) {
+      const float2 m4 = f2(-4.f, -4.f);
+      auto br = [&](int k) {
+        return __fadd2_rn(__ffma2_rn(m4, p, __fadd2_rn(xs(k), ys(k))), __ffma2_rn(p2, m1, zs(k)));
+      };
+      float2 a = __fmul2_rn(f2(K.cx[4], K.cx[4]), br(4));
+      a = __ffma2_rn(f2(K.cx[3], K.cx[3]), br(3), a);
+      a = __ffma2_rn(f2(K.cx[2], K.cx[2]), br(2), a);
+      a = __ffma2_rn(f2(K.cx[1], K.cx[1]), br(1), a);
+      lap[j] = a.x;
+      lap[j + 1] = a.y;
+      continue;
+    }
     float2 a = __fmul2_rn(f2(K.cx[4], K.cx[4]), __ffma2_rn(p2, m1, xs(4)));
     a = __ffma2_rn(f2(K.cx[3], K.cx[3]), __ffma2_rn(p2, m1, xs(3)), a);
     a = __ffma2_rn(f2(K.cx[2], K.cx[2]), __ffma2_rn(p2, m1, xs(2)), a);
@@ -105,7 +122,7 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   }
 }
 
-template <bool ADJ>
+template <bool ADJ, bool ISO>
 struct March3D {
   using S = Smem3D<ADJ>;
   static constexpr int NST = S::NST;
@@ -125,6 +142,8 @@ struct March3D {
   float gyv, gxv[4];
   const float* gz;       // shared gamma*dt per z level
   int pq, pst;           // producer: next sequence, its slot
+  int cslot, hslot;      // consumer: slots of sequences q and q - 4 (running, no division)
+  uint32_t cphase;       // consumer: (q / NST) & 1
   uint32_t pround;
   int ie_cur, ie_end, se_cur, se_end;  // point-list cursors (entries sorted by z)
   int inj_z, smp_z;                    // z of the entries under the cursors (INT_MAX: none left)
@@ -151,17 +170,17 @@ struct March3D {
   // Sequence q with the queue centre at compile-time index C = (q - 4) % 9.
   template <int C>
   __device__ __forceinline__ bool step(int q) {
-    const int slot = q % NST;
-    if (!mbar_wait_abortable(&full[slot], (uint32_t)((q / NST) & 1), P.status, abort_flag)) return false;
+    const int slot = cslot;
+    if (!mbar_wait_abortable(&full[slot], cphase, P.status, abort_flag)) return false;
     float* stage = sm + slot * S::STAGE;
     // the centre of halo plane q-4 enters the queue at index (C + 4) % 9
     Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX3 + lx + HALO);
     if (ADJ) QS[(C + 4) % 9] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX3 + lx + HALO);
     const int z = q - 2 * HALO;
     if (z >= 0) {
-      const float* hpl = sm + ((q - HALO) % NST) * S::STAGE;  // halo plane of level z
+      const float* hpl = sm + hslot * S::STAGE;  // halo plane of level z (sequence q - 4)
       float lap[4];
-      lap3<C>(hpl, Q, ly, lx, K, lap);
+      lap3<C, ISO>(hpl, Q, ly, lx, K, lap);
       const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX3 + lx);
       const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
       const float gzy = gz[z] + gyv;
@@ -211,7 +230,7 @@ struct March3D {
       }
       if (ADJ) {
         float lps[4];
-        lap3<C>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
+        lap3<C, ISO>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
         const float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (colv) {
           float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
@@ -239,13 +258,18 @@ struct March3D {
     // release the slot of sequence q-4: its halo plane served level q-8 above
     if (q >= HALO) {
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[(q - HALO) % NST]);
+      if (lane == 0) mbar_arrive(&empty[hslot]);
     }
+    if (++cslot == NST) {
+      cslot = 0;
+      cphase ^= 1u;
+    }
+    if (++hslot == NST) hslot = 0;
     return true;
   }
 };
 
-template <bool ADJ>
+template <bool ADJ, bool ISO>
 __global__ void __launch_bounds__(NTHREADS3, 1)
 step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_cc, const __grid_constant__ CUtensorMap tm_g, const Layout L,
@@ -259,7 +283,7 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST);
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  March3D<ADJ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
+  March3D<ADJ, ISO> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
   M.lane = tid & 31;
   M.ly = 2 * warp + (tid >> 4 & 1);
   M.x0 = blockIdx.x * TX3;
@@ -276,6 +300,9 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.pq = 0;
   M.pst = 0;
   M.pround = 0;
+  M.cslot = 0;
+  M.hslot = Smem3D<ADJ>::NST - HALO;  // (0 - 4) mod NST: first used at q = 4
+  M.cphase = 0;
 
   if (tid == 0) {
     tma_prefetch_desc(&tm_halo);
@@ -353,23 +380,30 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   if (rem > 7 && !M.template step<3>(q + 7)) return;
 }
 
+template <bool ADJ, bool ISO>
+static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
+                           const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, dim3 grid,
+                           cudaStream_t st) {
+  const size_t bytes = Smem3D<ADJ>::bytes(L.nzp);
+  cudaError_t e = cudaFuncSetAttribute(step3d_kernel<ADJ, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  step3d_kernel<ADJ, ISO><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
                           const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, int B,
                           cudaStream_t st) {
   const int nty = (L.nyp + TY3 - 1) / TY3;
   dim3 grid(P.ntx, nty, B);
-  if (adj) {
-    const size_t bytes = Smem3D<true>::bytes(L.nzp);
-    cudaError_t e = cudaFuncSetAttribute(step3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    step3d_kernel<true><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
-  } else {
-    const size_t bytes = Smem3D<false>::bytes(L.nzp);
-    cudaError_t e = cudaFuncSetAttribute(step3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    step3d_kernel<false><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
-  }
-  return cudaGetLastError();
+  // The one-bracket form serves the forward only: on the layered 3D batch
+  // it made the forward step 4 % faster and the adjoint step (two
+  // Laplacians) 2 % slower.
+  if (adj) return launch3<true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+  bool iso = true;
+  for (int k = 1; k <= 4; k++) iso = iso && K.cx[k] == K.cy[k] && K.cx[k] == K.cz[k];
+  return iso ? launch3<false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
+             : launch3<false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
 }
 
 }  // namespace fwi
