@@ -36,6 +36,12 @@ def _dev_ptr(t, dtype, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _numel(t, n, name):
+    """Every device buffer's size is checked here: the kernels trust it."""
+    if t.numel() != n:
+        raise ValueError("%s has %d elements (shape %s), expected %d" % (name, t.numel(), tuple(t.shape), n))
+
+
 def encode(seed, it, ns):
     """Supergather encoding of FWI iteration `it`: (perm int32[ns], w int8[ns]) (fwi_encode)."""
     perm = np.zeros(ns, np.int32)
@@ -66,6 +72,7 @@ class FWI:
         self._h = h
         self.ns, self.nr, self.nt = len(self._src), len(self._rec), int(grid["nt"])
         self.shape = (grid["nz"], grid["nx"]) if grid["ndim"] == 2 else (grid["nz"], grid["ny"], grid["nx"])
+        self.phys = int(np.prod(self.shape))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -91,8 +98,10 @@ class FWI:
         nsamp = vel.shape[0]
         keep = self._enc(nsamp, perm, w, sg_sizes)
         nsg = len(keep[2])
+        _numel(vel, nsamp * self.phys, "vel")
         if out is None:
             out = torch.empty((nsamp, nsg, self.nt, self.nr), device=vel.device, dtype=torch.float32)
+        _numel(out, nsamp * nsg * self.nt * self.nr, "out")
         check(lib().fwi_forward(self._h, _dev_ptr(vel, torch.float32, "vel"), nsamp, keep[3], keep[4], keep[5], nsg,
                                 _dev_ptr(out, torch.float32, "out"), _stream(stream)), "fwi_forward")
         return out
@@ -103,10 +112,14 @@ class FWI:
         nsamp = vel.shape[0]
         keep = self._enc(nsamp, perm, w, sg_sizes)
         nsg = len(keep[2])
+        _numel(vel, nsamp * self.phys, "vel")
+        _numel(d_obs, self.ns * self.nt * self.nr, "d_obs")
         if grad is None:
             grad = torch.empty_like(vel)
         if misfit is None:
             misfit = torch.empty(nsamp, device=vel.device, dtype=torch.float64)
+        _numel(grad, nsamp * self.phys, "grad")
+        _numel(misfit, nsamp, "misfit")
         check(lib().fwi_gradient(self._h, _dev_ptr(vel, torch.float32, "vel"), nsamp, keep[3], keep[4], keep[5],
                                  nsg, _dev_ptr(d_obs, torch.float32, "d_obs"), float(sigma), float(scale),
                                  _dev_ptr(grad, torch.float32, "grad"), _dev_ptr(misfit, torch.float64, "misfit"),
@@ -120,10 +133,12 @@ class FWI:
         nsamp = vel.shape[0]
         keep = self._enc(nsamp, perm, w, sg_sizes)
         nsg = len(keep[2])
+        _numel(vel, nsamp * self.phys, "vel")
         if tuple(d_cot.shape) != (nsamp, nsg, self.nt, self.nr):
             raise ValueError("d_cot must have shape %s, got %s" % ((nsamp, nsg, self.nt, self.nr), tuple(d_cot.shape)))
         if grad is None:
             grad = torch.empty_like(vel)
+        _numel(grad, nsamp * self.phys, "grad")
         check(lib().fwi_adjoint(self._h, _dev_ptr(vel, torch.float32, "vel"), nsamp, keep[3], keep[4], keep[5], nsg,
                                 _dev_ptr(d_cot, torch.float32, "d_cot"), _dev_ptr(grad, torch.float32, "grad"),
                                 _stream(stream)), "fwi_adjoint")
@@ -132,6 +147,9 @@ class FWI:
     def smooth_prior_grad(self, z, zref, lam, mu, grad, stream=None):
         """grad += gradient of the Gaussian smoothness prior (smooth_prior_grad)."""
         torch = _torch()
+        _numel(z, z.shape[0] * self.phys, "z")
+        _numel(zref, self.phys, "zref")
+        _numel(grad, z.shape[0] * self.phys, "grad")
         check(lib().smooth_prior_grad(self._h, _dev_ptr(z, torch.float32, "z"), _dev_ptr(zref, torch.float32, "zref"),
                                       z.shape[0], float(lam), float(mu), _dev_ptr(grad, torch.float32, "grad"),
                                       _stream(stream)), "smooth_prior_grad")
@@ -205,10 +223,15 @@ def residual_misfit_noalloc(d_pred, d_obs, perm, w, sg_sizes, sigma, scale=0.0, 
     perm = np.ascontiguousarray(np.broadcast_to(np.asarray(perm, np.int32), (nsamp, ns)))
     w = np.ascontiguousarray(np.broadcast_to(np.asarray(w, np.int8), (nsamp, ns)))
     sg = np.ascontiguousarray(sg_sizes, np.int32)
+    if len(sg) != nsg:
+        raise ValueError("d_pred has %d supergathers, sg_sizes %d" % (nsg, len(sg)))
+    _numel(d_obs, ns * nt * nr, "d_obs")
     if rhat is None:
         rhat = torch.empty_like(d_pred)
     if misfit is None:
         misfit = torch.empty(nsamp, device=d_pred.device, dtype=torch.float64)
+    _numel(rhat, d_pred.numel(), "rhat")
+    _numel(misfit, nsamp, "misfit")
     check(lib().fwi_residual_misfit_noalloc(
         _dev_ptr(d_pred, torch.float32, "d_pred"), _dev_ptr(d_obs, torch.float32, "d_obs"), nsamp, ns, nt, nr,
         perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),

@@ -262,3 +262,23 @@ def test_chunked_gradient_bit_identical(P, torch):
     torch.cuda.synchronize()
     assert small.plan_info()["samples_per_chunk"] == 1
     assert torch.equal(g1, g2) and torch.equal(m1, m2)
+
+
+def test_binding_rejects_mis_sized_buffers(P, torch):
+    # sizes are checked on the host before the library is called
+    w = synth.tiny2d(nt=50)
+    ctx = make_ctx(P, w, 2)
+    v = torch.full((1,) + w.shape, 2000.0, device="cuda")
+    perm, wt = P.encode(1, 0, w.ns)
+    d_obs = torch.zeros(w.ns, w.nt, w.nr, device="cuda")
+    with pytest.raises(ValueError, match="d_obs"):
+        ctx.gradient(v, perm, wt, [w.ns], d_obs[:, :-1], 1.0)
+    with pytest.raises(ValueError, match="vel"):
+        ctx.forward(v[:, :-1], perm, wt, [w.ns])
+    with pytest.raises(ValueError, match="out"):
+        ctx.forward(v, perm, wt, [w.ns], out=torch.empty(1, 1, w.nt, w.nr - 1, device="cuda"))
+    with pytest.raises(ValueError, match="grad"):
+        ctx.gradient(v, perm, wt, [w.ns], d_obs, 1.0, grad=torch.empty(2, *w.shape, device="cuda"))
+    with pytest.raises(ValueError, match="d_cot"):
+        ctx.adjoint(v, perm, wt, [w.ns], torch.zeros(1, 2, w.nt, w.nr, device="cuda"))
+    assert ctx.device_status() == 0

@@ -91,3 +91,19 @@ def test_cfl_bound_matches_stencil_spectrum():
     assert abs(rho - 6.501587) < 1e-6
     # isotropic 2D: v dt / h <= sqrt(4 / (2 rho))
     assert abs(np.sqrt(4 / (2 * rho)) - 0.5546) < 1e-4
+
+
+def test_noalloc_rejects_mis_sized_buffers(native):
+    # the binding checks every buffer's size before any device call: the
+    # kernels index them from the sizes they are given
+    import torch
+    import paper_2512_12797_gb300 as P
+    d_pred = torch.zeros(2, 3, 10, 4)
+    perm, w = P.encode(1, 0, 6)
+    with pytest.raises(ValueError, match="d_obs"):
+        P.residual_misfit_noalloc(d_pred, torch.zeros(6, 10, 5), perm, w, [2, 2, 2], 1.0)
+    with pytest.raises(ValueError, match="supergathers"):
+        P.residual_misfit_noalloc(d_pred, torch.zeros(6, 10, 4), perm, w, [3, 3], 1.0)
+    with pytest.raises(ValueError, match="misfit"):
+        P.residual_misfit_noalloc(d_pred, torch.zeros(6, 10, 4), perm, w, [2, 2, 2], 1.0,
+                                  misfit=torch.zeros(3, dtype=torch.float64))
