@@ -1,7 +1,7 @@
 // prior.h -- C ABI of the tensor-core kernels of the learned prior: the
 // network g_theta that predicts the clean model from a noisy one (Sec. 2.2,
 // eq. for x0-hat; trained on velocity-model patches, Sec. 3.1).  The network
-// is a small U-Net of 3x3 convolutions; these entry points run its
+// is a small U-Net of 3x3 (3D models: 3x3x3) convolutions; these entry points run its
 // contractions in BF16 with FP32 accumulation on the tensor cores.
 //
 // Conventions: all pointers are device pointers owned by the caller and
@@ -57,6 +57,25 @@ int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, 
 // {32, 64, 128, 256} or a multiple of 64.
 int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
                              int* status, void* stream);
+
+// 3D counterpart of prior_conv3x3_bf16 for volume patches (the prior of the
+// 3D models): same-size 3x3x3 cross-correlation with zero padding 1,
+//   Y[n][z][y][x][o] = sum_{dz,dy,dx in 0..2} sum_c Wt[o][dz*9+dy*3+dx][c] X[n][z+dz-1][y+dy-1][x+dx-1][c].
+//   X: [nimg][D][H][W][Cin] BF16 (NDHWC); Wt: [Cout][27][Cin] BF16;
+//   Y: [nimg][D][H][W][Cout] FP32 (y_bf16 = 0) or BF16 (y_bf16 = 1); bias: [Cout] FP32 or null.
+// Requires Cin % 64 == 0; Cout as prior_conv3x3_bf16; W a multiple of 128,
+// or a power of two < 128 with H * W a multiple of 128, or H and W powers of
+// two with H * W < 128 and D * H * W a multiple of 128.  The data gradient
+// is the same call with weights Wt'[c][26 - t][o] = Wt[o][t][c].
+int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D, int H, int W, int Cin, int Cout,
+                         int y_bf16, const float* bias, int relu, int* status, void* stream);
+
+// Weight gradient of prior_conv3x3x3_bf16, accumulated:
+//   dW[o][t][c] += sum_p dYt[o][p] * X27[t][c][p],
+// with X27 the input's 27 tap-shifted copies (t = dz*9 + dy*3 + dx) and the
+// other conventions of prior_conv3x3_wgrad_bf16 (splits <= 2427).
+int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, int P, int Cout, int Cin, int splits,
+                               int* status, void* stream);
 
 // Reads and clears the internal status word (synchronises the stream).
 int prior_last_status(void* stream);

@@ -19,7 +19,8 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradie
            "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error",
            "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking"]
 # every symbol prior.h declares
-PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_conv3x3_wgrad_bf16", "prior_last_status"]
+PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_conv3x3_wgrad_bf16", "prior_conv3x3x3_bf16",
+                 "prior_conv3x3x3_wgrad_bf16", "prior_last_status"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -83,6 +84,10 @@ _SIGS = {
                                           ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "prior_conv3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, _P, _P]),
+    "prior_conv3x3x3_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
+    "prior_conv3x3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _P, _P]),
     "prior_last_status": (ctypes.c_int, [_P]),
 }
 

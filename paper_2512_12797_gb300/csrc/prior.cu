@@ -19,7 +19,9 @@
 // The convolution (conv3x3_bf16) is the same pipeline with A gathered by TMA
 // from an NHWC activation tensor: for output rows y0.. and each tap (dy, dx)
 // and 64-channel block, the A tile is the input box shifted by (dy-1, dx-1);
-// coordinates outside the image read zeros, which is the padding.
+// coordinates outside the image read zeros, which is the padding.  The 3D
+// convolution (conv3x3x3_bf16, NDHWC volumes) takes a 5D box shifted by
+// (dz-1, dy-1, dx-1) for each of its 27 taps.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -80,6 +82,15 @@ __device__ __forceinline__ void tma4d(void* dst, const CUtensorMap* m, int c0, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma5d(void* dst, const CUtensorMap* m, int c0, int c1, int c2, int c3, int c4,
+                                      uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* m, int c0, int c1, int c2, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -89,10 +100,11 @@ __device__ __forceinline__ void tma3d(void* dst, const CUtensorMap* m, int c0, i
 }
 
 // Kernel modes: plain GEMM; 3x3 convolution (forward, and data gradient with
-// flipped weights); weight gradient of the 3x3 convolution: per tap a GEMM
-// over pixels, dY^T [Cout x P] times the tap-shifted input [Cin x P]^T, split
-// over pixel ranges and accumulated atomically in FP32.
-enum Mode { GEMM = 0, CONV = 1, WGRAD = 2 };
+// flipped weights); weight gradient of the 3x3 (or 3x3x3) convolution: per tap
+// a GEMM over pixels, dY^T [Cout x P] times the tap-shifted input [Cin x P]^T,
+// split over pixel ranges and accumulated atomically in FP32; 3x3x3
+// convolution of NDHWC volumes.
+enum Mode { GEMM = 0, CONV = 1, WGRAD = 2, CONV3 = 3 };
 
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA with
 // the 128-byte swizzle: rows of 64 BF16 (128 B), 8-row swizzle atoms 1024 B
@@ -162,7 +174,9 @@ struct Args {
   const float* bias; // [N] or null
   int relu;
   int H, W, Cin, TW, TH;  // convolution geometry (tile = TH rows x TW columns of one image)
-  int splits;        // weight gradient: pixel ranges per tap (grid z = 9 * splits)
+  int Dd, TD;        // 3D convolution: depth, and planes per tile (tile = TD x TH x TW)
+  int ntap;          // weight gradient: taps (9 or 27)
+  int splits;        // weight gradient: pixel ranges per tap (grid z = ntap * splits)
   int* status;
 };
 
@@ -193,8 +207,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
   // K blocks of this CTA: all of K, or (weight gradient) this split's 64-pixel chunks
   int kb0 = 0, nk = g.K / BK, tap = 0;
   if (MODE == WGRAD) {
-    tap = blockIdx.z % 9;
-    const int split = blockIdx.z / 9, chunks = g.K / BK;
+    tap = blockIdx.z % g.ntap;
+    const int split = blockIdx.z / g.ntap, chunks = g.K / BK;
     kb0 = (int)((long long)chunks * split / g.splits);
     nk = (int)((long long)chunks * (split + 1) / g.splits) - kb0;
   }
@@ -222,11 +236,21 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
   const uint32_t tbase = *tbase_s;
 
   // convolution tile: TH rows x TW columns of image img starting at (y0, x0)
-  int img = 0, y0 = 0, x0 = 0, ncb = 1;
+  // (3D: TD x TH x TW starting at (z0, y0, x0))
+  int img = 0, z0 = 0, y0 = 0, x0 = 0, ncb = 1;
   if (MODE == CONV) {
     const int hw = g.H * g.W;
     img = m0 / hw;
     const int rem = m0 - img * hw;
+    y0 = rem / g.W;
+    x0 = rem - y0 * g.W;
+    ncb = g.Cin / BK;
+  } else if (MODE == CONV3) {
+    const int hw = g.H * g.W, dhw = g.Dd * hw;
+    img = m0 / dhw;
+    int rem = m0 - img * dhw;
+    z0 = rem / hw;
+    rem -= z0 * hw;
     y0 = rem / g.W;
     x0 = rem - y0 * g.W;
     ncb = g.Cin / BK;
@@ -243,6 +267,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
         const int t = kb / ncb, cb = kb - t * ncb;
         const int dy = t / 3 - 1, dx = t % 3 - 1;
         tma4d(st, &tma_a, cb * BK, x0 + dx, y0 + dy, img, &full[s]);
+        tma2d(st + S::A_BYTES, &tma_b, kb * BK, n0, &full[s]);
+      } else if (MODE == CONV3) {
+        const int t = kb / ncb, cb = kb - t * ncb;  // tap t = dz*9 + dy*3 + dx
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        tma5d(st, &tma_a, cb * BK, x0 + dx, y0 + dy, z0 + dz, img, &full[s]);
         tma2d(st + S::A_BYTES, &tma_b, kb * BK, n0, &full[s]);
       } else if (MODE == WGRAD) {
         // 64-pixel chunk p0: dY^T rows m0.. and the tap's shifted input rows n0..
@@ -353,7 +382,7 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims
     s *= dims[i];
     strides[i] = s;
   }
-  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -376,7 +405,7 @@ int launch(const CUtensorMap& ma, const CUtensorMap& mb, const prior::Args& g, c
       return PRIOR_ERR_CUDA;
     attr = true;
   }
-  dim3 grid((g.M + prior::BM - 1) / prior::BM, g.N / BN, MODE == prior::WGRAD ? 9 * g.splits : 1);
+  dim3 grid((g.M + prior::BM - 1) / prior::BM, g.N / BN, MODE == prior::WGRAD ? g.ntap * g.splits : 1);
   kern<<<grid, 128, S::bytes, st>>>(ma, mb, g);
   return cudaGetLastError() == cudaSuccess ? PRIOR_OK : PRIOR_ERR_CUDA;
 }
@@ -463,30 +492,101 @@ int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, 
   return dispatch<prior::CONV>(bn, ma, mb, g, (cudaStream_t)stream);
 }
 
-int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
-                             int* status, void* stream) {
+}  // extern "C"
+
+namespace {
+
+int wgrad(const void* dYt, const void* Xs, float* dW, int P, int Cout, int Cin, int ntap, int splits, int* status,
+          void* stream) {
   const int bn = tile_n(Cin);
   const int mp = (Cout + prior::BM - 1) / prior::BM * prior::BM;
-  if (!dYt || !X9 || !dW || P <= 0 || P % prior::BK || Cout <= 0 || !bn || splits < 1 || splits > 4096)
+  if (!dYt || !Xs || !dW || P <= 0 || P % prior::BK || Cout <= 0 || !bn || splits < 1 || splits > 65535 / ntap)
     return PRIOR_ERR_ARG;
-  if (!aligned16(dYt) || !aligned16(X9) || !aligned16(dW)) return PRIOR_ERR_ARG;
+  if (!aligned16(dYt) || !aligned16(Xs) || !aligned16(dW)) return PRIOR_ERR_ARG;
   prior::Args g = {};
   g.M = Cout;
   g.N = Cin;
   g.K = P;
-  g.ldd = 9 * Cin;
+  g.ldd = ntap * Cin;
   g.D = dW;
   g.Cin = Cin;
+  g.ntap = ntap;
   g.splits = splits < P / prior::BK ? splits : P / prior::BK;
   g.status = status_ptr(status);
   if (!g.status) return PRIOR_ERR_CUDA;
   CUtensorMap ma, mb;
   const cuuint64_t da[2] = {(cuuint64_t)P, (cuuint64_t)mp};
   const cuuint32_t ba[2] = {prior::BK, prior::BM};
-  const cuuint64_t db[3] = {(cuuint64_t)P, (cuuint64_t)Cin, 9};
+  const cuuint64_t db[3] = {(cuuint64_t)P, (cuuint64_t)Cin, (cuuint64_t)ntap};
   const cuuint32_t bb[3] = {prior::BK, (cuuint32_t)bn, 1};
-  if (!make_map(&ma, dYt, 2, da, ba) || !make_map(&mb, X9, 3, db, bb)) return PRIOR_ERR_ARG;
+  if (!make_map(&ma, dYt, 2, da, ba) || !make_map(&mb, Xs, 3, db, bb)) return PRIOR_ERR_ARG;
   return dispatch<prior::WGRAD>(bn, ma, mb, g, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
+                             int* status, void* stream) {
+  return wgrad(dYt, X9, dW, P, Cout, Cin, 9, splits, status, stream);
+}
+
+int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D, int H, int W, int Cin, int Cout,
+                         int y_bf16, const float* bias, int relu, int* status, void* stream) {
+  const int bn = tile_n(Cout);
+  if (!X || !Wt || !Y || nimg <= 0 || D <= 0 || H <= 0 || W <= 0 || Cin <= 0 || Cin % prior::BK || !bn)
+    return PRIOR_ERR_ARG;
+  // a tile is 128 consecutive voxels of one volume: TW whole-width columns,
+  // TH whole rows, TD whole planes
+  int TW, TH, TD;
+  if (W >= 128) {
+    if (W % 128) return PRIOR_ERR_ARG;
+    TW = 128, TH = 1, TD = 1;
+  } else {
+    if (W & (W - 1)) return PRIOR_ERR_ARG;
+    TW = W;
+    if (H * W >= 128) {
+      TH = 128 / W, TD = 1;
+      if (H % TH) return PRIOR_ERR_ARG;
+    } else {
+      if (H & (H - 1)) return PRIOR_ERR_ARG;
+      TH = H, TD = 128 / (H * W);
+      if (D % TD) return PRIOR_ERR_ARG;
+    }
+  }
+  if (!aligned16(X) || !aligned16(Wt) || !aligned16(Y) || (bias && (reinterpret_cast<uintptr_t>(bias) & 3)))
+    return PRIOR_ERR_ARG;
+  prior::Args g = {};
+  g.M = nimg * D * H * W;
+  g.N = Cout;
+  g.K = 27 * Cin;
+  g.ldd = Cout;
+  g.D = Y;
+  g.d_bf16 = y_bf16 != 0;
+  g.bias = bias;
+  g.relu = relu != 0;
+  g.Dd = D;
+  g.H = H;
+  g.W = W;
+  g.Cin = Cin;
+  g.TW = TW;
+  g.TH = TH;
+  g.TD = TD;
+  g.status = status_ptr(status);
+  if (!g.status) return PRIOR_ERR_CUDA;
+  CUtensorMap ma, mb;
+  const cuuint64_t da[5] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)nimg};
+  const cuuint32_t ba[5] = {prior::BK, (cuuint32_t)TW, (cuuint32_t)TH, (cuuint32_t)TD, 1};
+  const cuuint64_t db[2] = {(cuuint64_t)(27 * Cin), (cuuint64_t)Cout};
+  const cuuint32_t bb[2] = {prior::BK, (cuuint32_t)bn};
+  if (!make_map(&ma, X, 5, da, ba) || !make_map(&mb, Wt, 2, db, bb)) return PRIOR_ERR_ARG;
+  return dispatch<prior::CONV3>(bn, ma, mb, g, (cudaStream_t)stream);
+}
+
+int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, int P, int Cout, int Cin, int splits,
+                               int* status, void* stream) {
+  return wgrad(dYt, X27, dW, P, Cout, Cin, 27, splits, status, stream);
 }
 
 int prior_last_status(void* stream) {

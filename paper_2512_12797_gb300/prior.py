@@ -1,5 +1,5 @@
 """Tensor-core building blocks of the learned prior g_theta (Sec. 2.2): the
-BF16 GEMM and the 3x3 convolution of include/prior.h.  Argument marshalling
+BF16 GEMM and the 3x3 and 3x3x3 convolutions of include/prior.h.  Argument marshalling
 only; every contraction runs in libfwi.so's tcgen05 kernels."""
 import torch
 
@@ -55,7 +55,7 @@ def last_status():
 
 
 def flip_weights(Wt):
-    """Weights of the data gradient: Wt'[c][8 - t][o] = Wt[o][t][c]."""
+    """Weights of the data gradient: Wt'[c][T - 1 - t][o] = Wt[o][t][c], T = 9 or 27 taps."""
     return Wt.flip(1).transpose(0, 2).contiguous()
 
 
@@ -96,6 +96,65 @@ def conv3x3_wgrad(dY, X, splits=None, out=None):
     rc = _native.lib().prior_conv3x3_wgrad_bf16(dYt.data_ptr(), X9.data_ptr(), out.data_ptr(), P, Cout, Cin,
                                                 splits, None, _stream())
     _check(rc, "prior_conv3x3_wgrad_bf16")
+    return out
+
+
+def conv3x3x3(X, Wt, bias=None, relu=False, out_bf16=True, out=None):
+    """Same-size 3x3x3 cross-correlation of volumes: X [n, D, H, W, Cin] BF16
+    (NDHWC), Wt [Cout, 27, Cin] BF16 (tap = dz*9 + dy*3 + dx), bias [Cout]
+    FP32; returns [n, D, H, W, Cout] in BF16 (or FP32)."""
+    n, D, H, W, Cin = X.shape
+    Cout = Wt.shape[0]
+    if out is None:
+        out = torch.empty((n, D, H, W, Cout), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=X.device)
+    rc = _native.lib().prior_conv3x3x3_bf16(X.data_ptr(), Wt.data_ptr(), out.data_ptr(), n, D, H, W, Cin, Cout,
+                                            int(out.dtype == torch.bfloat16),
+                                            bias.data_ptr() if bias is not None else None, int(relu), None,
+                                            _stream())
+    _check(rc, "prior_conv3x3x3_bf16")
+    return out
+
+
+def conv3x3x3_dgrad(dY, Wt, out_bf16=True):
+    """Gradient of conv3x3x3 with respect to its input: the same-size
+    convolution of dY with the flipped, transposed weights (flipping the tap
+    index t = dz*9 + dy*3 + dx reverses all three offsets)."""
+    return conv3x3x3(dY, flip_weights(Wt), out_bf16=out_bf16)
+
+
+def shifted_taps3(X):
+    """[27][Cin][P] BF16: X [n, D, H, W, Cin] shifted by (dz - 1, dy - 1, dx - 1)
+    for each tap t = dz*9 + dy*3 + dx, zero off the volume, channel-major over
+    voxels P = n*D*H*W."""
+    n, D, H, W, C = X.shape
+    Xp = torch.nn.functional.pad(X.permute(4, 0, 1, 2, 3), (1, 1, 1, 1, 1, 1))  # [C, n, D+2, H+2, W+2]
+    out = torch.empty((27, C, n * D * H * W), dtype=X.dtype, device=X.device)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                out[dz * 9 + dy * 3 + dx] = Xp[:, :, dz:dz + D, dy:dy + H, dx:dx + W].reshape(C, -1)
+    return out
+
+
+def conv3x3x3_wgrad(dY, X, splits=None, out=None):
+    """Gradient of conv3x3x3 with respect to its weights: dW [Cout, 27, Cin]
+    FP32 from the output gradient dY [n, D, H, W, Cout] and the input X."""
+    Cout = dY.shape[-1]
+    Cin = X.shape[-1]
+    P = dY.numel() // Cout
+    mp = (Cout + 127) // 128 * 128
+    dYt = torch.zeros((mp, P), dtype=torch.bfloat16, device=dY.device)
+    dYt[:Cout] = dY.reshape(P, Cout).t()
+    X27 = shifted_taps3(X.to(torch.bfloat16))
+    if out is None:
+        out = torch.zeros((Cout, 27, Cin), dtype=torch.float32, device=dY.device)
+    if splits is None:  # about two CTAs per SM over the (co, ci, tap) tiles
+        bn = Cin if Cin in (32, 64, 128, 256) else (128 if Cin % 128 == 0 else 64)
+        tiles = ((Cout + 127) // 128) * (Cin // bn) * 27
+        splits = max(1, min(P // 64, (2 * 152) // tiles))
+    rc = _native.lib().prior_conv3x3x3_wgrad_bf16(dYt.data_ptr(), X27.data_ptr(), out.data_ptr(), P, Cout, Cin,
+                                                  splits, None, _stream())
+    _check(rc, "prior_conv3x3x3_wgrad_bf16")
     return out
 
 

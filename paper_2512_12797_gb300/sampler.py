@@ -57,21 +57,25 @@ class GaussianPriorDenoiser:
     def __init__(self, mean, corr_cells=6.0, amp=1.0):
         import torch
         self.mean = mean
-        shape = mean.shape[-2:]
-        kz = torch.fft.fftfreq(shape[0], device=mean.device) * 2 * math.pi
-        kx = torch.fft.rfftfreq(shape[1], device=mean.device) * 2 * math.pi
-        k2 = kz[:, None] ** 2 + kx[None, :] ** 2
+        shape = tuple(mean.shape)  # the model's axes: (nz, nx) or (nz, ny, nx)
+        nd = len(shape)
+        k2 = 0.0
+        for a, n in enumerate(shape):
+            f = torch.fft.rfftfreq(n, device=mean.device) if a == nd - 1 else torch.fft.fftfreq(n, device=mean.device)
+            k = f * 2 * math.pi
+            k2 = k2 + (k ** 2).view([-1 if b == a else 1 for b in range(nd)])
         # spectral density per Fourier mode, normalised so the pointwise variance is amp^2
         S = (1.0 + k2 * corr_cells ** 2) ** -2
         S = S / S.mean() * amp ** 2
         self.S = S
+        self.dims = tuple(range(-len(shape), 0))
 
     def __call__(self, x_t, abar_t):
         import torch
         sig2 = (1.0 - abar_t) / abar_t
         y = x_t / math.sqrt(abar_t) - self.mean
-        Y = torch.fft.rfft2(y)
-        return self.mean + torch.fft.irfft2(Y * (self.S / (self.S + sig2)), s=y.shape[-2:])
+        Y = torch.fft.rfftn(y, dim=self.dims)
+        return self.mean + torch.fft.irfftn(Y * (self.S / (self.S + sig2)), s=y.shape[-len(self.dims):], dim=self.dims)
 
 
 def _rmse(v, truth):

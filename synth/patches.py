@@ -38,3 +38,27 @@ def geology_patches(n, size, seed, styles=("thrust", "salt", "arid"), crops_per_
             k += 1
         m += 1
     return out
+
+
+def volume_patches(n, size, seed, model_size=None, crops_per_model=16, vrange=(1500.0, 4500.0)):
+    """n volume patches [n, size, size, size] (float32, normalised units) for
+    the prior of the 3D models: random crops, with random flips of the two
+    horizontal axes, of seeded dipping-layer volumes offset by a planar fault
+    (the style of the 3D workload)."""
+    rng = np.random.default_rng(seed)
+    m = model_size or 2 * size
+    out = np.empty((n, size, size, size), np.float32)
+    k = 0
+    while k < n:
+        vol = normalize(models.layered_fault_3d(m, m, m, int(rng.integers(1 << 30)), vrange[0], vrange[1],
+                                                nlayers=int(rng.integers(4, 10))).astype(np.float64), *vrange)
+        for _ in range(min(crops_per_model, n - k)):
+            z0, y0, x0 = (int(rng.integers(0, m - size + 1)) for _ in range(3))
+            p = vol[z0:z0 + size, y0:y0 + size, x0:x0 + size]
+            if rng.integers(2):
+                p = p[:, ::-1, :]
+            if rng.integers(2):
+                p = p[:, :, ::-1]
+            out[k] = p
+            k += 1
+    return out

@@ -99,3 +99,54 @@ def test_conv3x3_wgrad_matches_oracle(P, n, H, W, Cin, Cout):
     # the tap layout: the centre tap alone is the plain channel correlation
     assert _rel(dW[:, 4].cpu().double().numpy(), ref[:, 4]) < 1e-4
     assert P.last_status() == 0
+
+
+# 3x3x3 convolution of volumes: the three tile forms (whole-width 128-voxel
+# rows; TH rows of a plane; TD whole planes) and the depth border
+@pytest.mark.parametrize("n,D,H,W,Cin,Cout", [(2, 4, 8, 16, 64, 64), (1, 8, 8, 8, 128, 32), (2, 16, 4, 4, 64, 128),
+                                              (1, 3, 2, 128, 64, 256), (2, 16, 16, 16, 64, 64)])
+def test_conv3x3x3_matches_oracle(P, n, D, H, W, Cin, Cout):
+    import torch
+    X, Wt = _bf16(torch, (n, D, H, W, Cin), 41 + D), _bf16(torch, (Cout, 27, Cin), 42 + Cout)
+    bias = torch.randn(Cout, generator=torch.Generator().manual_seed(43))
+    Y = P.conv3x3x3(X.cuda(), Wt.cuda(), bias=bias.cuda(), out_bf16=False)
+    ref = PO.conv3x3x3(X.float().numpy(), Wt.float().numpy()) + bias.double().numpy()
+    assert _rel(Y.cpu().double().numpy(), ref) < TOL
+    for sl in [(slice(None), 0), (slice(None), -1), (slice(None), slice(None), 0),
+               (slice(None), slice(None), slice(None), -1)]:
+        assert _rel(Y[sl].cpu().double().numpy(), ref[sl]) < TOL, sl
+    assert P.last_status() == 0
+
+
+def test_conv3x3x3_rejects_untileable_shapes(P):
+    import torch
+    from paper_2512_12797_gb300 import _native
+    L = _native.lib()
+    X = torch.zeros((1, 4, 4, 4, 64), dtype=torch.bfloat16, device="cuda")
+    Y = torch.zeros((1, 4, 4, 4, 64), dtype=torch.float32, device="cuda")
+    # 4 x 4 planes need 8 planes per tile: D = 4 is rejected; W = 24 is not a power of two
+    assert L.prior_conv3x3x3_bf16(X.data_ptr(), X.data_ptr(), Y.data_ptr(), 1, 4, 4, 4, 64, 64, 0, None, 0, None,
+                                  None) == -1
+    assert L.prior_conv3x3x3_bf16(X.data_ptr(), X.data_ptr(), Y.data_ptr(), 1, 1, 16, 24, 64, 64, 0, None, 0, None,
+                                  None) == -1
+
+
+@pytest.mark.parametrize("n,D,H,W,Cin,Cout", [(1, 4, 8, 16, 64, 64), (2, 8, 4, 4, 128, 64)])
+def test_conv3x3x3_dgrad_matches_oracle(P, n, D, H, W, Cin, Cout):
+    import torch
+    dY, Wt = _bf16(torch, (n, D, H, W, Cout), 51 + D), _bf16(torch, (Cout, 27, Cin), 52 + Cin)
+    dX = P.conv3x3x3_dgrad(dY.cuda(), Wt.cuda(), out_bf16=False)
+    ref = PO.conv3x3x3_dgrad(dY.float().numpy(), Wt.float().numpy())
+    assert _rel(dX.cpu().double().numpy(), ref) < TOL
+
+
+@pytest.mark.parametrize("n,D,H,W,Cin,Cout", [(1, 4, 8, 16, 64, 64), (2, 8, 8, 8, 128, 32)])
+def test_conv3x3x3_wgrad_matches_oracle(P, n, D, H, W, Cin, Cout):
+    import torch
+    dY, X = _bf16(torch, (n, D, H, W, Cout), 61 + W), _bf16(torch, (n, D, H, W, Cin), 62 + Cout)
+    dW = P.conv3x3x3_wgrad(dY.cuda(), X.cuda())
+    ref = PO.conv3x3x3_wgrad(dY.float().numpy(), X.float().numpy())
+    assert _rel(dW.cpu().double().numpy(), ref) < 1e-4
+    assert _rel(dW[:, 13].cpu().double().numpy(), ref[:, 13]) < 1e-4  # centre tap
+    assert _rel(dW[:, 0].cpu().double().numpy(), ref[:, 0]) < 1e-4    # corner tap
+    assert P.last_status() == 0
