@@ -159,27 +159,38 @@ def conv3x3x3_wgrad(dY, X, splits=None, out=None):
 
 
 def _main():
-    """Times one 3x3 convolution: python -m paper_2512_12797_gb300.prior [n H W Cin Cout]."""
+    """Times one convolution: python -m paper_2512_12797_gb300.prior [n H W Cin Cout]
+    (3x3) or [n D H W Cin Cout] (3x3x3)."""
     import sys
     from . import build
     build.build()
-    n, H, W, Cin, Cout = [int(a) for a in sys.argv[1:6]] if len(sys.argv) > 5 else (16, 128, 128, 128, 128)
-    X = torch.randn(n, H, W, Cin, device="cuda").to(torch.bfloat16)
-    Wt = torch.randn(Cout, 9, Cin, device="cuda").to(torch.bfloat16)
-    Y = torch.empty(n, H, W, Cout, device="cuda", dtype=torch.bfloat16)
+    a = [int(v) for v in sys.argv[1:]]
+    if len(a) == 6:
+        n, D, H, W, Cin, Cout = a
+        X = torch.randn(n, D, H, W, Cin, device="cuda").to(torch.bfloat16)
+        Wt = torch.randn(Cout, 27, Cin, device="cuda").to(torch.bfloat16)
+        Y = torch.empty(n, D, H, W, Cout, device="cuda", dtype=torch.bfloat16)
+        run, taps, name = (lambda: conv3x3x3(X, Wt, out=Y)), 27, "conv3x3x3 [%d, %d, %d, %d, %d]" % (n, D, H, W, Cin)
+        vox = n * D * H * W
+    else:
+        n, H, W, Cin, Cout = a if len(a) == 5 else (16, 128, 128, 128, 128)
+        X = torch.randn(n, H, W, Cin, device="cuda").to(torch.bfloat16)
+        Wt = torch.randn(Cout, 9, Cin, device="cuda").to(torch.bfloat16)
+        Y = torch.empty(n, H, W, Cout, device="cuda", dtype=torch.bfloat16)
+        run, taps, name = (lambda: conv3x3(X, Wt, out=Y)), 9, "conv3x3 [%d, %d, %d, %d]" % (n, H, W, Cin)
+        vox = n * H * W
     for _ in range(3):
-        conv3x3(X, Wt, out=Y)
+        run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(20):
-        conv3x3(X, Wt, out=Y)
+        run()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / 20
-    flops = 2.0 * n * H * W * 9 * Cin * Cout
-    print("conv3x3 [%d, %d, %d, %d] -> %d: %.3f ms, %.0f TFLOP/s, status %d"
-          % (n, H, W, Cin, Cout, ms, flops / ms / 1e9, last_status()))
+    flops = 2.0 * vox * taps * Cin * Cout
+    print("%s -> %d: %.3f ms, %.0f TFLOP/s, status %d" % (name, Cout, ms, flops / ms / 1e9, last_status()))
 
 
 if __name__ == "__main__":
