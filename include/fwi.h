@@ -122,6 +122,12 @@ int fwi_encode(uint64_t seed, uint64_t iter, int ns, int32_t* perm_out, int8_t* 
  *   perm, w  host   [nsamp][ns]          encoding of each sample (as fwi_encode)
  *   sg_sizes host   [nsg]                shots per supergather, sum <= ns
  *   d_pred   device [nsamp][nsg][nt][nr] output records
+ * Every velocity must lie in (0, sponge_vmax], the bound the stability
+ * condition was checked against in fwi_create; any other value (or a NaN)
+ * records FWI_ERR_CFL in the device status word (fwi_last_device_status) and
+ * that call's outputs are not valid (the 2D step kernels leave at their next
+ * dependency check; the 3D ones finish their bounded loops).  The same holds
+ * for fwi_gradient and fwi_adjoint.
  */
 int fwi_forward(fwi_ctx* ctx, const float* vel, int nsamp, const int32_t* perm,
                 const int8_t* w, const int32_t* sg_sizes, int nsg, float* d_pred, void* stream);
