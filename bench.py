@@ -348,8 +348,8 @@ def native_arm(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded thrust-belt models, random records)",
-           "config": {"workload": w.name, "grid": [w.nz, w.nx], "h_m": w.hx, "nb": w.nb, "nt": w.nt,
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded %s models, random records)" % w.name,
+           "config": {"workload": w.name, "grid": list(w.shape), "h_m": w.hx, "nb": w.nb, "nt": w.nt,
                       "sources": w.ns, "receivers": w.nr, "samples": nsamp, "supergathers": sg,
                       "wavefields_per_launch": B, "padded_points": w.padded_points,
                       "parallelism": "replicas" if world > 1 else "single-gpu",
