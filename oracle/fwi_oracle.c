@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int ndim, nz, ny, nx;
@@ -391,4 +394,16 @@ double or_smooth_prior(const or_grid* g, const double* z, const double* zref, do
                 }
     }
     return phi;
+}
+
+/* Threads of the spatial loops: n > 0 sets them; returns the number in use
+ * (1 without OpenMP).  Timing only: results do not depend on it. */
+int or_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

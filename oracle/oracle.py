@@ -56,6 +56,7 @@ def load(path):
     G = ctypes.POINTER(_Grid)
     sig = {
         "or_npad": (ctypes.c_long, [G]),
+        "or_threads": (ctypes.c_int, [ctypes.c_int]),
         "or_cell_volume": (ctypes.c_double, [G]),
         "or_pad_index": (ctypes.c_long, [G, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "or_sponge": (None, [G, _D]),
@@ -237,6 +238,13 @@ def fold_gradient(g, v, gc):
 
 
 # --------------------------------------------------------------- encoding --
+
+def threads(n=0):
+    """Threads of the oracle's spatial loops: n > 0 sets them; returns the
+    number in use.  Results do not depend on it (each loop writes disjoint
+    elements, and the reductions are serial)."""
+    return int(lib().or_threads(int(n)))
+
 
 def mix64(x):
     return int(lib().or_mix64(ctypes.c_uint64(x & (2 ** 64 - 1))))
