@@ -244,6 +244,23 @@ int fwi_last_device_status(fwi_ctx* ctx, void* stream);
 int fwi_plan_info(fwi_ctx* ctx, int* segment_len, int* nsegments, int64_t* recomputed_steps,
                   int* slots_used, int* slots_available);
 
+/* Checkpoint schedule of fwi_gradient for nt steps and a pool of `slots`
+ * wavefield slots (host only, no device work; the paper is silent on
+ * checkpointing).  Slot 0 always holds zeros; the forward pass keeps
+ * checkpoint pairs and the last segment's snapshots, and each earlier segment
+ * is recomputed from its checkpoint before its adjoint steps.  Returns the
+ * plan's segment length, number of segments, recomputed steps and slots used,
+ * the number of step descriptors in *nsteps and, if desc_out is not null,
+ * the descriptors in launch order as rows of 7 ints
+ *   {launch, kind (0 forward, 1 adjoint), cur, prev, out, snap, t}:
+ * a forward step t reads p^t (cur, with halo) and p^{t-1} (prev) and writes
+ * p^{t+1}; an adjoint step t reads q^{t+2} (cur, with halo), q^{t+3} (prev)
+ * and the snapshot p^t (snap, with halo) and writes q^{t+1}.  All steps with
+ * the same launch index run in one launch in 2D.  FWI_ERR_OOM if no plan fits
+ * `slots`, FWI_ERR_ARG if cap < *nsteps. */
+int fwi_checkpoint_schedule(int nt, int64_t slots, int32_t* desc_out, int cap, int* nsteps, int* segment_len,
+                            int* nsegments, int64_t* recomputed, int* slots_used);
+
 /* Samples per chunk of the last fwi_gradient call.  When the checkpoint plan
  * of all nsamp*nsg wavefields does not fit the workspace (large 3D batches),
  * fwi_gradient processes the samples in chunks, choosing the chunk size that

@@ -17,7 +17,7 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradie
            "renoise",
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
            "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error",
-           "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking"]
+           "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking", "fwi_checkpoint_schedule"]
 # every symbol prior.h declares
 PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_conv3x3_wgrad_bf16", "prior_conv3x3x3_bf16",
                  "prior_conv3x3x3_wgrad_bf16", "prior_last_status"]
@@ -55,6 +55,10 @@ _SIGS = {
     "fwi_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, _I32P, _I8P, _I32P, ctypes.c_int, _P, _P]),
     "fwi_gradient": (ctypes.c_int, [_P, _P, ctypes.c_int, _I32P, _I8P, _I32P, ctypes.c_int, _P, ctypes.c_double,
                                     ctypes.c_double, _P, _P, _P]),
+    "fwi_checkpoint_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _I32P, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_int)]),
     "fwi_adjoint": (ctypes.c_int, [_P, _P, ctypes.c_int, _I32P, _I8P, _I32P, ctypes.c_int, _P, _P, _P]),
     "langevin_step": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, _P]),

@@ -835,15 +835,37 @@ void fwi_destroy(fwi_ctx* C) {
   delete C;
 }
 
-// Forward steps 0..nt-1 with the slots of the checkpoint plan, or of a
-// three-slot ring when no snapshots are kept.
-static void append_forward_descs(fwi_ctx* C, const Plan* plan) {
-  for (int n = 0; n < C->g.nt; n++) {
-    if (plan)
-      C->descs.push_back(make_desc(plan->fslot(n), plan->fslot(n - 1), plan->fslot(n + 1), Plan::ZERO, n));
-    else
-      C->descs.push_back(make_desc(n <= 0 ? 0 : 1 + n % 3, n - 1 <= 0 ? 0 : 1 + (n - 1) % 3, 1 + (n + 1) % 3,
-                                   Plan::ZERO, n));
+// Forward steps 0..nt-1 of fwi_forward on a three-slot ring (no snapshots kept).
+static void append_forward_descs(fwi_ctx* C) {
+  for (int n = 0; n < C->g.nt; n++)
+    C->descs.push_back(make_desc(n <= 0 ? 0 : 1 + n % 3, n - 1 <= 0 ? 0 : 1 + (n - 1) % 3, 1 + (n + 1) % 3,
+                                 Plan::ZERO, n));
+}
+
+// Step descriptors of one gradient chunk in launch order: the first forward
+// pass (steps 0..nt-1), then per segment j from the last, its recomputed
+// forward steps and its adjoint steps; rc_* / ad_* give each segment's two
+// phases as (offset, count) into descs.
+static void gradient_descs(const Plan& plan, int nt, std::vector<StepDesc>& descs, std::vector<int>& rc_off,
+                           std::vector<int>& rc_n, std::vector<int>& ad_off, std::vector<int>& ad_n) {
+  descs.clear();
+  for (int n = 0; n < nt; n++)
+    descs.push_back(make_desc(plan.fslot(n), plan.fslot(n - 1), plan.fslot(n + 1), Plan::ZERO, n));
+  rc_off.assign(plan.jL + 1, 0);
+  rc_n.assign(plan.jL + 1, 0);
+  ad_off.assign(plan.jL + 1, 0);
+  ad_n.assign(plan.jL + 1, 0);
+  for (int j = plan.jL; j >= 0; j--) {
+    const int m0 = j * plan.K, m1 = std::min((j + 1) * plan.K, nt);  // snapshots m0..m1-1
+    rc_off[j] = (int)descs.size();
+    if (j < plan.jL)
+      for (int n = m0; n <= m1 - 2; n++)
+        descs.push_back(make_desc(plan.rslot(j, n), plan.rslot(j, n - 1), plan.rslot(j, n + 1), Plan::ZERO, n));
+    rc_n[j] = (int)descs.size() - rc_off[j];
+    ad_off[j] = (int)descs.size();
+    for (int k = m1; k >= m0 + 1; k--)
+      descs.push_back(make_desc(plan.qslot(k + 1), plan.qslot(k + 2), plan.qslot(k), plan.snap(j, k - 1), k - 1));
+    ad_n[j] = (int)descs.size() - ad_off[j];
   }
 }
 
@@ -890,7 +912,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   C->last_was_gradient = false;
   prof_mark(C, 0, st);
   C->descs.clear();
-  append_forward_descs(C, nullptr);
+  append_forward_descs(C);
   if ((rc = upload_descs(C, st)) != FWI_OK) return rc;
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, d_pred, st)) != FWI_OK) return rc;
@@ -927,23 +949,8 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
 
   prof_mark(C, 0, st);
-  // step descriptors of the whole chunk: forward, then per segment j (last
-  // first) the recomputed forward steps and the adjoint steps
-  C->descs.clear();
-  append_forward_descs(C, &plan);
-  std::vector<int> rc_off(plan.jL + 1), rc_n(plan.jL + 1), ad_off(plan.jL + 1), ad_n(plan.jL + 1);
-  for (int j = plan.jL; j >= 0; j--) {
-    const int m0 = j * plan.K, m1 = std::min((j + 1) * plan.K, nt);  // snapshots m0..m1-1
-    rc_off[j] = (int)C->descs.size();
-    if (j < plan.jL)
-      for (int n = m0; n <= m1 - 2; n++)
-        C->descs.push_back(make_desc(plan.rslot(j, n), plan.rslot(j, n - 1), plan.rslot(j, n + 1), Plan::ZERO, n));
-    rc_n[j] = (int)C->descs.size() - rc_off[j];
-    ad_off[j] = (int)C->descs.size();
-    for (int k = m1; k >= m0 + 1; k--)
-      C->descs.push_back(make_desc(plan.qslot(k + 1), plan.qslot(k + 2), plan.qslot(k), plan.snap(j, k - 1), k - 1));
-    ad_n[j] = (int)C->descs.size() - ad_off[j];
-  }
+  std::vector<int> rc_off, rc_n, ad_off, ad_n;
+  gradient_descs(plan, nt, C->descs, rc_off, rc_n, ad_off, ad_n);
   if ((rc = upload_descs(C, st)) != FWI_OK) return rc;
 
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
@@ -1139,6 +1146,48 @@ int fwi_last_device_status(fwi_ctx* C, void* stream) {
   CK(cudaMemcpy(&v, C->status, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemset(C->status, 0, 4));
   return v;
+}
+
+int fwi_checkpoint_schedule(int nt, int64_t slots, int32_t* desc_out, int cap, int* nsteps, int* segment_len,
+                            int* nsegments, int64_t* recomputed, int* slots_used) {
+  if (nt <= 0 || !nsteps) return FWI_ERR_ARG;
+  Plan plan;
+  if (!make_plan(nt, (long long)slots, &plan)) return FWI_ERR_OOM;
+  std::vector<StepDesc> d;
+  std::vector<int> rc_off, rc_n, ad_off, ad_n;
+  gradient_descs(plan, nt, d, rc_off, rc_n, ad_off, ad_n);
+  *nsteps = (int)d.size();
+  if (segment_len) *segment_len = plan.K;
+  if (nsegments) *nsegments = plan.jL + 1;
+  if (recomputed) *recomputed = plan.recompute;
+  if (slots_used) *slots_used = plan.slots;
+  if (!desc_out) return FWI_OK;
+  if (cap < (int)d.size()) return FWI_ERR_ARG;
+  // launch of each descriptor, as gradient_chunk issues them
+  std::vector<int> launch(d.size(), 0), kind(d.size(), 0);
+  int l = 1;
+  for (int j = plan.jL; j >= 0; j--) {
+    if (rc_n[j] > 0) {
+      for (int i = rc_off[j]; i < rc_off[j] + rc_n[j]; i++) launch[i] = l;
+      l++;
+    }
+    for (int i = ad_off[j]; i < ad_off[j] + ad_n[j]; i++) {
+      launch[i] = l;
+      kind[i] = 1;
+    }
+    l++;
+  }
+  for (size_t i = 0; i < d.size(); i++) {
+    int32_t* r = desc_out + 7 * i;
+    r[0] = launch[i];
+    r[1] = kind[i];
+    r[2] = d[i].cur;
+    r[3] = d[i].prev;
+    r[4] = d[i].out;
+    r[5] = d[i].snap;
+    r[6] = d[i].t;
+  }
+  return FWI_OK;
 }
 
 int fwi_plan_info(fwi_ctx* C, int* K, int* nseg, int64_t* rec, int* used, int* avail) {
