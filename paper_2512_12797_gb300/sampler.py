@@ -17,10 +17,15 @@ counterpart of the Adam refinement of Sec. 3.2), so each step moves an
 element by about eta m/s; the independent noise has standard deviation nu
 m/s.
 
-The clean-model predictor here is the exact MMSE denoiser of a stationary
-Gaussian prior on the normalised model (diagonal in Fourier space).  It
-stands in for the trained network g_theta of Sec. 2.2, which this package
-does not provide; any callable (x_t, abar_t) -> x0^ can be passed instead.
+The clean-model predictor is any callable (x_t, abar_t) -> x0^: the learned
+network g_theta of Sec. 2.2 (unet.UNetDenoiser, unet3d.UNet3DDenoiser on the
+tensor-core kernels) or, by default, the exact MMSE denoiser of a stationary
+Gaussian prior on the normalised model (diagonal in Fourier space).
+
+The encoded sampler can stop before a level and resume from the returned
+state: every random draw after the initial one is counter-based (encodings
+from (seed, step), Langevin noise from (seed, step), re-noise from (seed,
+level)), so a resumed run is bit-identical to an uninterrupted one.
 
 Cost is counted as eq. pde-count: one forward and one adjoint solve per
 supergather per gradient evaluation.
@@ -97,6 +102,13 @@ class RMSPreconditioner:
         self.v = torch.zeros_like(like)
         self.alpha, self.eps, self.n = alpha, eps, 0
 
+    def state_dict(self):
+        return {"v": self.v.clone(), "n": self.n}
+
+    def load_state_dict(self, st):
+        self.v.copy_(st["v"])
+        self.n = int(st["n"])
+
     def __call__(self, g):
         self.n += 1
         self.v.mul_(self.alpha).addcmul_(g, g, value=1.0 - self.alpha)
@@ -115,6 +127,14 @@ class AdamState:
         self.v = torch.zeros_like(like)
         self.b1, self.b2, self.eps, self.n = beta1, beta2, eps, 0
 
+    def state_dict(self):
+        return {"m": self.m.clone(), "v": self.v.clone(), "n": self.n}
+
+    def load_state_dict(self, st):
+        self.m.copy_(st["m"])
+        self.v.copy_(st["v"])
+        self.n = int(st["n"])
+
     def __call__(self, g):
         self.n += 1
         self.m.mul_(self.b1).add_(g, alpha=1.0 - self.b1)
@@ -122,6 +142,12 @@ class AdamState:
         mhat = self.m / (1.0 - self.b1 ** self.n)
         vhat = self.v / (1.0 - self.b2 ** self.n)
         g.copy_(mhat / (vhat.sqrt() + self.eps))
+
+
+def _sync(t):
+    import torch
+    if t.is_cuda:
+        torch.cuda.synchronize(t.device)
 
 
 def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, prior_lam=0.0, prior_mu=0.0,
@@ -150,7 +176,7 @@ def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, pri
     zref = v0.mean(0) if zref is None else zref
     grad = torch.empty_like(z)
     precond = RMSPreconditioner(z)
-    torch.cuda.synchronize()
+    _sync(z)
     t0 = time.perf_counter()
     solves = 0
     for k in range(steps):
@@ -168,12 +194,13 @@ def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, pri
         if (k + 1) % record_every == 0:
             hist_r.append(_rmse(z.mean(0), truth))
             hist_s.append(solves)
-    torch.cuda.synchronize()
+    _sync(z)
     return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0, "samples": z}
 
 
 def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_start, stride, K, eta, nu, vmin, vmax,
-                              sigma, denoiser=None, seed=0, renoise_on=True, refine="langevin"):
+                              sigma, denoiser=None, seed=0, renoise_on=True, refine="langevin", state=None,
+                              stop_at=None):
     """Decoupled encoded-shot diffusion sampler (Sec. 2.3, Algorithm table).
 
     refine: "langevin" -- K Langevin steps per guided level (Sec. 2.3 (ii));
@@ -188,6 +215,11 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
     `stride`-th level, each with K Langevin steps on the encoded likelihood
     with the given supergather sizes.  Returns dict(rmse, solves, seconds,
     samples) with the posterior-mean RMSE after every guided level.
+
+    Checkpoint and resume: with stop_at = t the run stops before level t and
+    returns samples=None and a "state" (plain tensors and numbers, e.g. for
+    torch.save); passing it back as state= with the same other arguments
+    continues at level t, bit-identically to an uninterrupted run.
     """
     import torch
     beta, abar = ddpm_schedule()
@@ -195,24 +227,40 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
     x_init = normalize(v_init, vmin, vmax)
     if denoiser is None:
         denoiser = GaussianPriorDenoiser(x_init)
-    gen = torch.Generator(device=dev).manual_seed(seed)
-    t = t_start
-    x_t = (math.sqrt(abar[t - 1]) * x_init[None] +
-           math.sqrt(1 - abar[t - 1]) * torch.randn((nsamp,) + tuple(v_init.shape), device=dev, generator=gen))
-    x_t = x_t.contiguous()
-    grad = torch.empty_like(x_t)
     if refine not in ("langevin", "adam"):
         raise ValueError("refine must be 'langevin' or 'adam'")
+    run_key = [int(seed), int(nsamp), [int(v) for v in sg_sizes], int(t_start), int(stride), int(K), refine,
+               bool(renoise_on)]
+    shape = (nsamp,) + tuple(v_init.shape)
+    if state is None:
+        gen = torch.Generator(device=dev).manual_seed(seed)
+        x_t = (math.sqrt(abar[t_start - 1]) * x_init[None] +
+               math.sqrt(1 - abar[t_start - 1]) * torch.randn(shape, device=dev, generator=gen)).contiguous()
+    else:
+        if state["run"] != run_key:
+            raise ValueError("state was saved by a run with other arguments: %s" % (state["run"],))
+        x_t = state["x_t"].to(dev).clone().contiguous()
+    grad = torch.empty_like(x_t)
     precond = RMSPreconditioner(x_t) if refine == "langevin" else AdamState(x_t)
     step_nu = nu if refine == "langevin" else 0.0
-    hist_r, hist_s = [_rmse(v_init, truth)], [0]
-    solves = 0
-    it = 0
+    if state is None:
+        hist_r, hist_s = [_rmse(v_init, truth)], [0]
+        solves, it, t_first = 0, 0, t_start
+    else:
+        precond.load_state_dict({k: (v.to(dev) if hasattr(v, "to") else v) for k, v in state["precond"].items()})
+        hist_r, hist_s = list(state["rmse"]), list(state["solves"])
+        solves, it, t_first = int(state["solves_total"]), int(state["it"]), int(state["t"])
     nsg = len(sg_sizes)
-    torch.cuda.synchronize()
+    _sync(x_t)
     t0 = time.perf_counter()
     z = None
-    for t in range(t_start, 0, -1):
+    for t in range(t_first, 0, -1):
+        if stop_at is not None and t == stop_at:
+            _sync(x_t)
+            st = {"run": run_key, "t": t, "x_t": x_t.clone(), "it": it, "solves_total": solves,
+                  "rmse": list(hist_r), "solves": list(hist_s), "precond": precond.state_dict()}
+            return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0, "samples": None,
+                    "state": st}
         x0 = denoiser(x_t, abar[t - 1]).clamp(-1.0, 1.0)
         if t % stride == 0 or t == 1:
             z = unnormalize(x0, vmin, vmax).contiguous()
@@ -235,6 +283,6 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
                 x_t = renoise(x_t.contiguous(), x0.contiguous(), abar[t - 1], abar[t - 2], beta[t - 1], seed + 2, t)
             else:
                 x_t = (math.sqrt(abar[t - 2]) * x0).contiguous()
-    torch.cuda.synchronize()
+    _sync(x_t)
     return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0,
             "samples": unnormalize(x0, vmin, vmax)}
