@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fwi_internal.cuh"
 
 using namespace fwi;
@@ -108,6 +110,28 @@ bool make_plan(int nt, long long avail, Plan* out) {
 }
 
 constexpr int kTuneSteps = 6;  // steps per autotuner timing launch
+
+// NVTX ranges (profiler annotations; no-ops when no tool is attached): one
+// for the call, and inside it one for each phase in turn.  The destructor
+// closes whatever is open, so early error returns stay balanced.
+struct Ranges {
+  int depth = 0;
+  explicit Ranges(const char* call) { push(call); }
+  void push(const char* name) {
+    nvtxRangePushA(name);
+    depth++;
+  }
+  void phase(const char* name) {
+    if (depth > 1) {
+      nvtxRangePop();
+      depth--;
+    }
+    push(name);
+  }
+  ~Ranges() {
+    while (depth-- > 0) nvtxRangePop();
+  }
+};
 
 struct Entry {  // a point on the padded grid with a record column and amplitude
   int z, y, x, col;
@@ -897,6 +921,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   int rc = validate_call(C, vel, nsamp, perm, w, sg, nsg);
   if (rc != FWI_OK) return rc;
   if (!d_pred) return FWI_ERR_ARG;
+  Ranges nv("fwi_forward");
   cudaStream_t st = (cudaStream_t)stream;
   const int B = nsamp * nsg;
   long long nslots;
@@ -948,6 +973,8 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
 
+  Ranges nv("gradient chunk");
+  nv.phase("forward");
   prof_mark(C, 0, st);
   std::vector<int> rc_off, rc_n, ad_off, ad_n;
   gradient_descs(plan, nt, C->descs, rc_off, rc_n, ad_off, ad_n);
@@ -960,6 +987,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
+  nv.phase(cot ? "cotangent" : "residual and misfit");
   if (cot) {  // the given cotangent is the adjoint source
     CK(cudaMemcpyAsync(C->dpred, cot, (size_t)B * nt * nr * 4, cudaMemcpyDeviceToDevice, st));
   } else {  // residual (rhat overwrites dpred) and misfit
@@ -973,6 +1001,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   }
   prof_mark(C, 2, st);
 
+  nv.phase("reverse sweep");
   // reverse sweep: recompute each earlier segment, then the adjoint steps
   StepParams F = base_params(C, B, nsg);  // recompute: sources only, no sampling
   F.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
@@ -1005,6 +1034,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   }
   C->launches[2] += adj_launch;
   prof_mark(C, 3, st);
+  nv.phase("source imaging and fold");
   CK(launch_source_imaging(B, nsg, nt, C->Emax, C->qsrc, C->wav,
                            reinterpret_cast<const int*>(C->dlist + cl.src_cnt),
                            reinterpret_cast<const long long*>(C->dlist + cl.src_pos),
@@ -1029,6 +1059,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
 static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w,
                           const int32_t* sg, int nsg, const float* d_obs, const float* cot, double sigma_y,
                           double scale, float* grad, double* misfit, cudaStream_t st) {
+  Ranges nv(cot ? "fwi_adjoint" : "fwi_gradient");
   const int nt = C->g.nt;
   // Samples per chunk: the whole batch when its checkpoint plan fits the pool,
   // otherwise the chunk size that minimises (chunks) x (2 nt + recomputed
