@@ -282,3 +282,33 @@ def test_binding_rejects_mis_sized_buffers(P, torch):
     with pytest.raises(ValueError, match="d_cot"):
         ctx.adjoint(v, perm, wt, [w.ns], torch.zeros(1, 2, w.nt, w.nr, device="cuda"))
     assert ctx.device_status() == 0
+
+
+def test_degenerate_calls_are_rejected_and_leave_the_context_usable(P, torch):
+    # empty batches, empty or oversized supergathers, shot ids outside the
+    # geometry and weights other than +-1 are refused on the host
+    # (FWI_ERR_ARG); the next valid call matches a fresh context bit for bit
+    w = synth.tiny2d(nt=60)
+    ctx = make_ctx(P, w, 2)
+    v = torch.tensor(synth.models.random_smooth_model(w.shape, 3, 1500, 2500)[None]).cuda()
+    perm, wt = P.encode(2, 0, w.ns)
+    bad_calls = [
+        lambda: ctx.forward(v[:0], perm, wt, [w.ns]),            # no samples
+        lambda: ctx.forward(v, perm, wt, []),                    # no supergathers
+        lambda: ctx.forward(v, perm, wt, [w.ns, 0]),             # an empty supergather
+        lambda: ctx.forward(v, perm, wt, [w.ns, 1]),             # more shots than the geometry has
+        lambda: ctx.forward(v, perm, wt, [1, 1, 1]),             # more wavefields than the context holds
+        lambda: ctx.forward(v, np.array([0, 1, 2, w.ns], np.int32), wt, [w.ns]),   # shot id out of range
+        lambda: ctx.forward(v, np.array([0, 1, 2, -1], np.int32), wt, [w.ns]),     # negative shot id
+        lambda: ctx.forward(v, perm, np.array([1, -1, 0, 1], np.int8), [w.ns]),    # weight not +-1
+    ]
+    for i, call in enumerate(bad_calls):
+        with pytest.raises(P.FwiError) as e:
+            call()
+        assert e.value.code == -1, (i, e.value.code)
+    d = ctx.forward(v, perm, wt, [2, 2])
+    fresh = make_ctx(P, w, 2)
+    d_fresh = fresh.forward(v, perm, wt, [2, 2])
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    assert torch.equal(d, d_fresh)
