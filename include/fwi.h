@@ -60,7 +60,9 @@ typedef enum {
     FWI_ERR_CUDA = -4,       /* a CUDA runtime call failed */
     FWI_ERR_NONFINITE = -5,  /* device status: misfit was NaN or Inf */
     FWI_ERR_TIMEOUT = -6,    /* device status: a bounded wait ran out */
-    FWI_ERR_BOUNDS = -7      /* device status: an index check failed */
+    FWI_ERR_BOUNDS = -7      /* device status: an index check failed (reserved for a debug build
+                                with device index checks; this version sets it nowhere: every
+                                index the kernels use is validated on the host) */
 } fwi_status;
 
 /* Physical grid, time axis, wavelet and sponge.  ny/hy are ignored in 2D. */
