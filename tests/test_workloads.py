@@ -73,3 +73,26 @@ def test_random_records_are_seeded():
     a, b = synth.random_records(w, 3), synth.random_records(w, 3)
     assert a.shape == (w.ns, w.nt, w.nr) and a.dtype == np.float32 and np.array_equal(a, b)
     assert not np.array_equal(a, synth.random_records(w, 4))
+
+
+def test_training_patches_are_seeded_normalised_and_shaped():
+    import synth.patches as SP
+    a = SP.geology_patches(40, 32, 3)
+    assert a.shape == (40, 32, 32) and a.dtype == np.float32
+    assert a.min() >= -1.0 and a.max() <= 1.0 and np.array_equal(a, SP.geology_patches(40, 32, 3))
+    v = SP.volume_patches(20, 16, 4)
+    assert v.shape == (20, 16, 16, 16) and v.min() >= -1.0 and v.max() <= 1.0
+    assert np.array_equal(v, SP.volume_patches(20, 16, 4)) and not np.array_equal(v, SP.volume_patches(20, 16, 5))
+
+
+def test_2d_prior_tile_shape_is_tileable_at_every_level():
+    from paper_2512_12797_gb300 import unet
+    for H, W in [(187, 801), (210, 676), (201, 1001), (64, 64), (101, 101)]:
+        Hp, Wp = unet.tile_shape(H, W)
+        assert Hp >= H and Wp >= W
+        for lev in range(3):
+            h, wl = Hp >> lev, Wp >> lev
+            assert Hp % (1 << lev) == 0 and Wp % (1 << lev) == 0
+            assert wl % 128 == 0 or (wl <= 128 and wl & (wl - 1) == 0)   # the 3x3 kernel's width rule
+            assert (h * min(wl, 128)) % 128 == 0                          # whole 128-pixel tiles
+    assert unet.tile_shape(187, 801) == (188, 1024)
