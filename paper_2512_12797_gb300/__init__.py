@@ -75,9 +75,17 @@ class FWI:
         self.phys = int(np.prod(self.shape))
 
     def close(self):
+        """Frees the context's device workspace (also on garbage collection)."""
         if getattr(self, "_h", None):
             lib().fwi_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:
