@@ -442,3 +442,22 @@ def test_ddpm_schedule_definition():
     beta, abar = O.ddpm_schedule()
     assert len(beta) == 1000 and math.isclose(beta[0], 1e-4) and math.isclose(beta[-1], 0.02)
     assert math.isclose(abar[9], float(np.prod(1 - beta[:10])), rel_tol=1e-14)
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    # the OpenMP loops write disjoint elements and every reduction is serial,
+    # so the timing baseline's thread setting cannot change a result
+    w_ = synth.tiny2d(nt=80, ns=4)
+    g = O.Grid.from_workload(w_)
+    v = synth.models.random_smooth_model(w_.shape, 2, 1500, 2500)
+    perm, w = O.encode(1, 1, w_.ns)
+    d_obs = synth.random_records(w_, 4)
+    n0 = O.threads()
+    try:
+        O.threads(1)
+        one = O.gradient(g, v, w_.src, w_.rec, d_obs, perm, w, [2, 2], 0.5)
+        O.threads(max(2, n0))
+        many = O.gradient(g, v, w_.src, w_.rec, d_obs, perm, w, [2, 2], 0.5)
+    finally:
+        O.threads(n0)
+    assert one[0] == many[0] and np.array_equal(one[1], many[1])
