@@ -350,6 +350,49 @@ void or_langevin(double* z, const double* grad, long n, double eta, double nu, d
     }
 }
 
+/* Preconditioned Langevin step.  The paper's conclusion (Sec. 5) requires the
+ * refinement to stay a stochastic Langevin step "with noise matched to any
+ * preconditioning"; this is the diagonal preconditioner of preconditioned
+ * SGLD (Li et al. 2016, RMSprop second moment) with the noise scaled by the
+ * square root of the same preconditioner, and, with a first moment, the Adam
+ * update the paper's experiments use for deterministic refinement (Sec. 3.2).
+ * For each of nsamp samples of `per` elements, at step number k:
+ *   v_i <- alpha v_i + (1 - alpha) g_i^2
+ *   m_i <- beta1 m_i + (1 - beta1) g_i                  (only when m != NULL)
+ *   vh_i = v_i / (1 - alpha^k),  mh_i = m_i / (1 - beta1^k)   (k = 0: no correction)
+ *   r    = sqrt(mean over the sample of vh_i)
+ *   G_i  = 1 / (sqrt(vh_i) + eps r)                     (0 where the denominator is 0)
+ *   d_i  = mh_i when m != NULL, else g_i
+ *   z_i <- clamp(z_i - eta G_i d_i + nu sqrt(G_i) xi_i, vmin, vmax)
+ * xi_i = gauss(seed, counter, s * per + i).  With nu = sqrt(2 eta) and a
+ * constant G the chain targets exp(-Phi) up to the O(eta) bias of the
+ * unadjusted step (Sec. 2.3 (ii)); another nu is the paper's independent
+ * noise scale (Sec. 2.3, modification of DAPS). */
+void or_langevin_precond(double* z, const double* grad, double* v, double* m, int nsamp, long per,
+                         double alpha, double beta1, double eps, long k, double eta, double nu,
+                         double vmin, double vmax, uint64_t seed, uint64_t counter) {
+    double cv = k > 0 ? 1.0 - pow(alpha, (double)k) : 1.0;
+    double cm = k > 0 ? 1.0 - pow(beta1, (double)k) : 1.0;
+    for (int s = 0; s < nsamp; s++) {
+        long o = (long)s * per;
+        double msum = 0.0;
+        for (long i = 0; i < per; i++) {
+            double g = grad[o + i];
+            v[o + i] = alpha * v[o + i] + (1.0 - alpha) * g * g;
+            if (m) m[o + i] = beta1 * m[o + i] + (1.0 - beta1) * g;
+            msum += v[o + i] / cv;
+        }
+        double r = sqrt(msum / (double)per);
+        for (long i = 0; i < per; i++) {
+            double den = sqrt(v[o + i] / cv) + eps * r;
+            double G = den > 0.0 ? 1.0 / den : 0.0;
+            double d = m ? m[o + i] / cm : grad[o + i];
+            double x = z[o + i] - eta * G * d + nu * sqrt(G) * or_gauss(seed, counter, (uint64_t)(o + i));
+            z[o + i] = x < vmin ? vmin : (x > vmax ? vmax : x);
+        }
+    }
+}
+
 /* DDPM re-noise (Sec. 2.3 (iii), posterior mean and variance):
  *   btilde = (1 - abar_prev) / (1 - abar_t) * beta_t
  *   mu     = sqrt(abar_prev) beta_t / (1 - abar_t) x0 + sqrt(1 - beta_t)(1 - abar_prev)/(1 - abar_t) x_t

@@ -10,6 +10,7 @@ steps in the order the paper states them:
   encoded misfit               1/(2 sigma_y^2) ||d~ - F~(x)||^2                   (Sec. 2.1)
   unbiased gradient            (N_s / m) grad Phi~                                (Sec. 2.1)
   Langevin refinement          z - eta grad + nu xi                               (Sec. 2.3 (ii))
+  preconditioned refinement    z - eta G d + nu sqrt(G) xi                        (Sec. 2.3 (ii), Sec. 5)
   DDPM re-noise                N(mu~_t(x_t, x0), beta~_t I)                       (Sec. 2.3 (iii))
 
 Readings where the paper is silent are listed in the C file header.  The
@@ -75,6 +76,10 @@ def load(path):
         "or_gauss": (ctypes.c_double, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]),
         "or_langevin": (None, [_D, _D, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64]),
+        "or_langevin_precond": (None, [_D, _D, _D, _D, ctypes.c_int, ctypes.c_long, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_long, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.c_uint64]),
         "or_renoise": (None, [_D, _D, _D, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.c_uint64, ctypes.c_uint64]),
         "or_smooth_prior": (ctypes.c_double, [G, _D, _D, ctypes.c_double, ctypes.c_double, _D]),
@@ -360,6 +365,20 @@ def langevin(z, grad, eta, nu, vmin, vmax, seed, counter):
     lib().or_langevin(_dp(z), _dp(_f64(grad)), z.size, eta, nu, vmin, vmax, ctypes.c_uint64(seed),
                       ctypes.c_uint64(counter))
     return z
+
+
+def langevin_precond(z, grad, v, m, eta, nu, vmin, vmax, seed, counter, k, alpha=0.9, beta1=0.9, eps=1e-3):
+    """Preconditioned Langevin step (noise matched to the preconditioner) on
+    z [nsamp][...]: returns (z, v, m) updated copies; m None = no first moment."""
+    z = _f64(z).copy()
+    nsamp = z.shape[0]
+    per = z.size // nsamp
+    v = _f64(v).copy()
+    m = None if m is None else _f64(m).copy()
+    lib().or_langevin_precond(_dp(z), _dp(_f64(grad)), _dp(v), _dp(m) if m is not None else None, nsamp, per,
+                              alpha, beta1, eps, int(k), eta, nu, vmin, vmax, ctypes.c_uint64(seed),
+                              ctypes.c_uint64(counter))
+    return z, v, m
 
 
 def renoise(x_t, x0, abar_t, abar_prev, beta_t, seed, counter):

@@ -34,6 +34,13 @@ MUTANTS = [
      P.test_renoise_preserves_ddpm_marginal),
     ("langevin_ascends", "z[i] - eta * grad[i]", "z[i] + eta * grad[i]",
      P.test_langevin_ula_stationary_variance),
+    ("precond_noise_not_matched", "nu * sqrt(G) * or_gauss", "nu * or_gauss",
+     P.test_precond_langevin_matched_noise_stationary_variance),
+    ("precond_rms_of_first_sample_only", "double r = sqrt(msum / (double)per);",
+     "static double r0; double r = s == 0 ? (r0 = sqrt(msum / (double)per)) : r0;",
+     P.test_precond_langevin_closed_form_steps_and_per_sample_scale),
+    ("precond_no_bias_correction", "double cv = k > 0 ? 1.0 - pow(alpha, (double)k) : 1.0;", "double cv = 1.0;",
+     P.test_precond_langevin_closed_form_steps_and_per_sample_scale),
     ("shuffle_off_by_one", "(unsigned __int128)(i + 1)) >> 64", "(unsigned __int128)(i)) >> 64",
      P.test_fisher_yates_uniform_chi2),
     ("sponge_sign_flipped", "pn[k] = (2.0 * p[k] - (1.0 - gam[k] * dt) * pm[k]", "pn[k] = (2.0 * p[k] - (1.0 + gam[k] * dt) * pm[k]",

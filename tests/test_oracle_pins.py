@@ -390,6 +390,72 @@ def test_langevin_clamps_and_descends():
     assert out.tolist() == [1500.0, 2000.0, 3050.0]
 
 
+def test_precond_langevin_matched_noise_stationary_variance():
+    # Quadratic Phi = z^2/(2 s^2) with a constant diagonal preconditioner G
+    # (alpha = 1 freezes v; k = 0 drops the bias correction; eps = 0 makes
+    # G = 1/sqrt(v)).  z' = z - eta G z/s^2 + sqrt(2 eta) sqrt(G) xi is the
+    # unadjusted chain with step eta G, whose stationary variance is
+    # s^2 / (1 - eta G/(2 s^2)) (Sec. 5: noise matched to the preconditioning).
+    # Three groups with G = 0.25, 1, 3 give three different variances; noise
+    # that ignored G, or a G taken from v instead of sqrt(v), misses them.
+    s2, eta, n = 4.0, 1.0, 20000
+    Gs = [0.25, 1.0, 3.0]
+    v = np.concatenate([np.full(n, 1.0 / G ** 2) for G in Gs])[None]
+    z = np.zeros_like(v)
+    acc = []
+    for k in range(400):
+        z, v, _ = O.langevin_precond(z, z / s2, v, None, eta, math.sqrt(2 * eta), -1e30, 1e30, 21, k, k=0,
+                                     alpha=1.0, eps=0.0)
+        if k >= 100:
+            acc.append([z[0, j * n:(j + 1) * n].var() for j in range(3)])
+    got = np.mean(acc, axis=0)
+    for G, var in zip(Gs, got):
+        expect = s2 / (1 - eta * G / (2 * s2))
+        assert abs(var - expect) < 0.03 * expect, (G, var, expect)
+
+
+def test_precond_langevin_closed_form_steps_and_per_sample_scale():
+    # A constant gradient g gives, after k steps, v_k = (1 - alpha^k) g^2 and
+    # m_k = (1 - beta1^k) g, so the bias-corrected moments are exactly g^2 and
+    # g and every step moves z by -eta g / (|g| + eps RMS(g)), with RMS taken
+    # over the sample.  Sample 1's gradient is 1000 x sample 0's: both move
+    # alike (the preconditioner removes the gradient's scale, per sample).
+    rng = np.random.default_rng(5)
+    g0 = rng.normal(0, 1, 50)
+    g0[7] = 0.0
+    grad = np.stack([g0, 1000.0 * g0])
+    eta, eps = 5.0, 1e-3
+    for use_m in (False, True):
+        z = np.full((2, 50), 2500.0)
+        v = np.zeros_like(z)
+        m = np.zeros_like(z) if use_m else None
+        expect = z.copy()
+        for k in range(1, 4):
+            z, v, m = O.langevin_precond(z, grad, v, m, eta, 0.0, 0.0, 1e9, 3, k, k=k, alpha=0.999, beta1=0.9,
+                                         eps=eps)
+            for s in range(2):
+                r = np.sqrt(np.mean(grad[s] ** 2))
+                expect[s] -= eta * grad[s] / (np.abs(grad[s]) + eps * r)
+            assert np.max(np.abs(z - expect)) < 1e-9, (use_m, k)
+        assert np.max(np.abs(z[0] - z[1])) < 1e-9
+        assert z[0, 7] == 2500.0
+
+
+def test_precond_langevin_reduces_to_plain_step():
+    # G = 1 everywhere (v = 1 frozen, no bias correction, eps = 0): the
+    # preconditioned step is the plain Langevin step with the same noise.
+    rng = np.random.default_rng(6)
+    z = rng.normal(2500, 300, (2, 40))
+    g = rng.normal(0, 1, (2, 40))
+    got, _, _ = O.langevin_precond(z, g, np.ones_like(z), None, 7.0, 3.0, 1600.0, 3400.0, 8, 9, k=0, alpha=1.0,
+                                   eps=0.0)
+    ref = O.langevin(z.ravel(), g.ravel(), 7.0, 3.0, 1600.0, 3400.0, 8, 9).reshape(2, 40)
+    assert np.max(np.abs(got - ref)) < 1e-9
+    # a sample whose gradient and moment are all zero does not move (G = 0, no NaN)
+    zz, _, _ = O.langevin_precond(z, np.zeros_like(z), np.zeros_like(z), None, 7.0, 3.0, 0.0, 1e9, 8, 9, k=1)
+    assert np.array_equal(zz, z)
+
+
 def test_renoise_at_first_level_returns_x0():
     # abar_0 = 1: beta~_1 = 0 and mu~_1 = x0 exactly.
     beta, abar = O.ddpm_schedule()
