@@ -200,17 +200,17 @@ int smooth_prior_grad(fwi_ctx* ctx, const float* z, const float* zref, int nsamp
 /*
  * Encoded residual and misfit for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an interface for users of the library.
- * Some callers must not call cudaMalloc: code that runs while a stream is
- * being captured (allocation is not permitted during capture), plug-ins whose
- * host application owns the device memory pool, and latency-bound loops that
- * cannot absorb the implicit synchronisation of an allocation.  This entry
- * point allocates nothing and needs no context; it computes what fwi_gradient
- * computes between its forward and adjoint passes:
+ * Some callers must not call cudaMalloc: plug-ins whose host application owns
+ * the device memory pool and forbids allocations of its own, and tight loops
+ * that cannot absorb the implicit device synchronisation of an allocation.
+ * This entry point allocates nothing and needs no context; it computes what
+ * fwi_gradient computes between its forward and adjoint passes:
  *   rhat[b][n][r] = (d_pred[b][n][r] - sum_{i in B_b} w_i d_obs[i][n][r]) / sigma_y^2
  *   misfit[s]     = scale * sum_j 1/(2 sigma_y^2) ||d~_j - F~_j||^2
  *   d_pred  device [nsamp][nsg][nt][nr]   encoded predicted records (e.g. from fwi_forward)
  *   d_obs   device [ns][nt][nr]           observed single-shot records
- *   perm, w host [nsamp][ns], sg_sizes host [nsg]: the encoding, as in fwi_gradient
+ *   perm, w host [nsamp][ns], sg_sizes host [nsg]: the encoding, as in fwi_gradient;
+ *           copied before the call returns, so they may be freed afterwards
  *   rhat    device [nsamp][nsg][nt][nr]   output (may equal d_pred: computed in place)
  *   misfit  device [nsamp] double         output
  *   scale   <= 0 selects N_s / sum(sg_sizes)
@@ -219,10 +219,12 @@ int smooth_prior_grad(fwi_ctx* ctx, const float* z, const float* zref, int nsamp
  * the library holds until the process exits; calls whose scratch would exceed
  * it (roughly nsamp*nsg*512 + nsamp*ns*13 bytes) return FWI_ERR_ARG.  The
  * first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it, so make the first call
- * on a device before any stream capture.  Every call reuses the same array,
- * so calls that overlap on the GPU (on different streams or from different
- * host threads) race; serialise them.  Non-finite values show up in misfit.
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call reuses the same array and keeps the
+ * last call's contents, so calls that overlap on the GPU (on different streams
+ * or from different host threads) race; serialise them.  A non-finite value
+ * in d_pred or d_obs makes the misfit non-finite; rhat can overflow to +-Inf
+ * when |r| / sigma_y^2 exceeds the FP32 range.
  */
 #define FWI_NOALLOC_MAX_BYTES (1u << 20)
 int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_obs, int nsamp, int ns, int nt, int nr,

@@ -7,7 +7,25 @@
 
 namespace fwi {
 
-static inline int grid_for(long long n, int cap) { long long b = (n + 255) / 256; return (int)(b < cap ? (b > 0 ? b : 1) : cap); }
+// Blocks of 256 threads for a grid-stride loop over n elements: enough for
+// every element, at most `per_sm` resident blocks on each SM of the current
+// device (the SM count is queried once per device).
+static int num_sms() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64 && cached[dev] > 0) return cached[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev < 64) cached[dev] = n;
+  return n;
+}
+
+static inline int grid_for(long long n, int per_sm) {
+  const long long cap = (long long)num_sms() * per_sm;
+  const long long b = (n + 255) / 256;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
 
 // ------------------------------------------------------------------ setup --
 
@@ -39,7 +57,7 @@ __global__ void expand_kernel(const Layout L, const float* __restrict__ vel, int
 cudaError_t launch_expand(const Layout& L, const float* vel, int nsamp, double dt, const float* gtab, float* c,
                           float vmax_cfl, int* status, cudaStream_t st) {
   const long long n = (long long)L.nzp * L.nyp * L.nxp * nsamp;
-  const int blocks = grid_for(n, 152 * 32);
+  const int blocks = grid_for(n, 32);
   expand_kernel<<<blocks, 256, 0, st>>>(L, vel, nsamp, dt, gtab, c, vmax_cfl, status);
   return cudaGetLastError();
 }
@@ -68,7 +86,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // r = d_pred - sum_{i in B_b} w_i d_obs_i (encoded observed data formed on the
 // fly), rhat = r / sigma^2 (adjoint source), and per-block partial sums of r^2
 // in FP64 (fixed reduction order: deterministic).
-__global__ void residual_kernel(int nt, int nr, const float* __restrict__ dpred, const float* __restrict__ dobs,
+// rhat may alias dpred (fwi_gradient computes in place): each element is read
+// and then written by the same thread, and neither pointer is __restrict__.
+__global__ void residual_kernel(int nt, int nr, const float* dpred, const float* __restrict__ dobs,
                                 const int* __restrict__ shot_off, const int* __restrict__ shot_id,
                                 const float* __restrict__ shot_w, double inv_sigma2, float* rhat, double* part,
                                 int nblk) {
@@ -120,7 +140,7 @@ __global__ void misfit_kernel(int nsg, const double* __restrict__ part, int nblk
     v = warp_sum(v);
     if (threadIdx.x == 0) {
       misfit[s] = factor * v;
-      if (!isfinite(v)) atomicCAS(status, 0, (int)FWI_ERR_NONFINITE);
+      if (status && !isfinite(v)) atomicCAS(status, 0, (int)FWI_ERR_NONFINITE);
     }
   }
 }
@@ -204,7 +224,7 @@ __global__ void finalize_kernel(const Layout L, const float* __restrict__ vel, c
 cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp, int g_per_sample,
                             double scale, float* grad, cudaStream_t st) {
   const long long n = L.phys * nsamp;
-  const int blocks = grid_for(n, 152 * 32);
+  const int blocks = grid_for(n, 32);
   finalize_kernel<<<blocks, 256, 0, st>>>(L, vel, G, nsamp, g_per_sample, scale, grad);
   return cudaGetLastError();
 }
@@ -246,7 +266,7 @@ cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, d
     };
     return m(seed ^ m(counter));
   }();
-  const int blocks = grid_for(n, 152 * 16);
+  const int blocks = grid_for(n, 16);
   langevin_kernel<<<blocks, 256, 0, st>>>(z, g, n, eta, nu, vmin, vmax, key);
   return cudaGetLastError();
 }
@@ -268,7 +288,7 @@ cudaError_t launch_renoise(float* xp, const float* xt, const float* x0, long lon
     return x ^ (x >> 31);
   };
   const uint64_t key = m(seed ^ m(counter));
-  const int blocks = grid_for(n, 152 * 16);
+  const int blocks = grid_for(n, 16);
   renoise_kernel<<<blocks, 256, 0, st>>>(xp, xt, x0, n, c0, ct, sd, key);
   return cudaGetLastError();
 }
@@ -307,7 +327,7 @@ __global__ void prior_kernel(const Layout L, const float* __restrict__ z, const 
 cudaError_t launch_prior(const Layout& L, const float* z, const float* zref, int nsamp, double lam, double mu,
                          double hz, double hy, double hx, float* grad, cudaStream_t st) {
   const long long n = L.phys * nsamp;
-  const int blocks = grid_for(n, 152 * 16);
+  const int blocks = grid_for(n, 16);
   prior_kernel<<<blocks, 256, 0, st>>>(L, z, zref, nsamp, lam, mu, 1.0 / (hz * hz), 1.0 / (hy * hy),
                                        1.0 / (hx * hx), grad);
   return cudaGetLastError();

@@ -1,15 +1,16 @@
 // noalloc.cu -- fwi_residual_misfit_noalloc: the encoded residual and misfit
 // for callers that must not allocate device memory.
 //
-// Its scratch (FP64 per-block partial sums, the copied encoding, the derived
-// shot lists and a status word) lives in one file-scope device array of
+// Its scratch (FP64 per-block partial sums, the copied encoding and the
+// derived shot lists) lives in one file-scope device array of
 // FWI_NOALLOC_MAX_BYTES, which every GPU that loads this library keeps until
 // the process exits.  Host code cannot use the array's name as a device
 // address, so on the first call on each device (with that device current) the
 // address is looked up once with cudaGetSymbolAddress and cached.  Every call
-// reuses the same array: whatever must start at zero is cleared per call,
-// and calls that overlap on the GPU (different streams, or different host
-// threads) race on it.
+// reuses the same array and keeps the last call's contents; each call writes
+// every piece of it before reading it (the per-block partial sums are stores,
+// not accumulations), so nothing needs clearing.  Calls that overlap on the
+// GPU (different streams, or different host threads) race on it.
 #include <string.h>
 
 #include "fwi_internal.cuh"
@@ -87,8 +88,7 @@ extern "C" int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_o
   const size_t o_perm = o_w + up256((size_t)(nsamp * tot) * 4);
   const size_t o_wt = o_perm + up256((size_t)nsamp * ns * 4);
   const size_t o_sg = o_wt + up256((size_t)nsamp * ns);
-  const size_t o_status = o_sg + up256((size_t)nsg * 4);
-  const size_t need = o_status + 256;
+  const size_t need = o_sg + up256((size_t)nsg * 4);
   if (need > (size_t)FWI_NOALLOC_MAX_BYTES || B > (1 << 30)) return FWI_ERR_ARG;
 
   void* base = nullptr;
@@ -98,8 +98,7 @@ extern "C" int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_o
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemcpyAsync(S + o_perm, perm, (size_t)nsamp * ns * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(S + o_wt, w, (size_t)nsamp * ns, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(S + o_sg, sg_sizes, (size_t)nsg * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(S + o_status, 0, 256, st) != cudaSuccess)
+      cudaMemcpyAsync(S + o_sg, sg_sizes, (size_t)nsg * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FWI_ERR_CUDA;
   noalloc_lists_kernel<<<(int)((B + 127) / 128), 128, 0, st>>>(
       nsamp, ns, nsg, reinterpret_cast<const int*>(S + o_perm), reinterpret_cast<const int8_t*>(S + o_wt),
@@ -112,7 +111,7 @@ extern "C" int fwi_residual_misfit_noalloc(const float* d_pred, const float* d_o
                            rhat, reinterpret_cast<double*>(S + o_part), NOALLOC_NBLK, st) != cudaSuccess)
     return FWI_ERR_CUDA;
   if (fwi::launch_misfit(nsamp, nsg, reinterpret_cast<const double*>(S + o_part), NOALLOC_NBLK, scale * 0.5 * inv_s2,
-                         misfit, reinterpret_cast<int*>(S + o_status), st) != cudaSuccess)
+                         misfit, nullptr, st) != cudaSuccess)
     return FWI_ERR_CUDA;
   return FWI_OK;
 }
