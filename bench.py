@@ -4,15 +4,21 @@
 One step is one pass of the whole hot path over one batch: supergather
 encoding of every posterior sample (host), the encoded misfit and velocity
 gradient of every sample over all its supergathers (forward, residual,
-adjoint, imaging; fwi_gradient), a Langevin refinement step (langevin_step)
-and a DDPM re-noise draw (renoise).  The default workload is the 2D
-thrust-belt case: 801 x 187 nodes at 25 m, 20-cell sponge, 100 sources,
-400 receivers, 8 Hz Ricker, dt 2 ms, 2000 steps, 16 posterior samples x 5
-supergathers of 20 +-1-encoded shots (80 wavefields per launch).
+adjoint, imaging; fwi_gradient), a preconditioned Langevin refinement step
+(langevin_step_precond) and a DDPM re-noise draw (renoise).
+
+The headline workload is the largest one, the 3D layered volume:
+256 x 256 x 128 nodes at 20 m, 20-cell sponge (296 x 296 x 168 padded,
+14.7 M points), 64 sources as 4 +-1-encoded supergathers of 16, 64 x 64
+receivers, 5 Hz Ricker, dt 1.5 ms, 1500 steps, 8 posterior samples, FP32
+wavefields with checkpointing.  The 2D thrust-belt batch (801 x 187 at 25 m,
+100 sources, 400 receivers, 2000 steps, 16 samples x 5 supergathers of 20)
+is timed as an extra, and so is the posterior-samples-per-hour comparison at
+equal model RMSE on the thrust-belt geometry.
 
 Metric: useful updates 2 x padded points x nt x wavefields per step / time.
-Inputs (about 0.2 GB of wavefields per time step, 130 GB of snapshots per
-step) are far larger than L2, so no flush is needed between steps.
+Inputs (0.5 GB of wavefields per 3D time step, hundreds of GB of snapshots
+per step) are far larger than L2, so no flush is needed between steps.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the baseline arm; it is not a GPU implementation).
@@ -33,9 +39,10 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "thrust2d"
+WORKLOAD = "layered3d"
 METRIC = "FWI fwd+adj Gpt/s (encoded gradient, grid-point updates/s)"
 UNIT = "Gpt/s"
+ORACLE_NT_3D = 40   # steps of the bounded 3D oracle sample (rate per step is what is reported)
 
 
 def _peaks():
@@ -132,18 +139,20 @@ def bytes_per_update(nsg, ndim=2):
     return {"forward": 12.0 + 4.0 / nsg, "adjoint": 16.0 + 12.0 / nsg}
 
 
-def run_oracle_sample(w, nsg_sample, seed):
-    """FP64 oracle gradient for one sample over nsg_sample supergathers at full nt."""
+def oracle_sample(w, nsg_sample, seed, nt=None):
+    """FP64 oracle gradient for one sample over nsg_sample supergathers, on the
+    first nt steps (all when None).  Returns (Gpt/s, seconds, workload run)."""
     import oracle as O
-    g = O.Grid.from_workload(w)
-    v = synth.initial_model(w)
-    d = synth.random_records(w, seed, nshots=w.ns)
-    perm, wt = O.encode(seed, 0, w.ns)
-    sg = w.sg_sizes[:nsg_sample]
+    wr = synth.WORKLOADS[w.name](nt=nt) if nt else w
+    g = O.Grid.from_workload(wr)
+    v = synth.initial_model(wr)
+    d = synth.random_records(wr, seed, nshots=wr.ns)
+    perm, wt = O.encode(seed, 0, wr.ns)
+    sg = wr.sg_sizes[:nsg_sample]
     t = time.perf_counter()
-    O.gradient(g, v, w.src, w.rec, d, perm, wt, sg, 1.0, scale=1.0)
+    O.gradient(g, v, wr.src, wr.rec, d, perm, wt, sg, 1.0, scale=1.0)
     dt = time.perf_counter() - t
-    return 2.0 * w.padded_points * w.nt * nsg_sample / dt / 1e9, dt
+    return 2.0 * wr.padded_points * wr.nt * nsg_sample / dt / 1e9, dt, wr
 
 
 def oracle_threads():
@@ -152,22 +161,30 @@ def oracle_threads():
     return O.threads()
 
 
+def _oracle_sample_plan(w):
+    """(supergathers, steps, description) of the bounded oracle sample of w."""
+    if w.ndim == 3:
+        return 1, ORACLE_NT_3D, ("%s: 1 sample x 1 supergather of %d shots, first %d of %d steps, fwd+adj+imaging, "
+                                 "FP64; the rate per step is extrapolated to the full run"
+                                 % (w.name, w.sg_sizes[0], ORACLE_NT_3D, w.nt))
+    return 1, None, ("%s: 1 sample x 1 supergather of %d shots, full %d steps, fwd+adj+imaging, FP64"
+                     % (w.name, w.sg_sizes[0], w.nt))
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     w = synth.WORKLOADS[args.workload]()
-    nsg_sample = 1
+    nsg_sample, nt, sample = _oracle_sample_plan(w)
     for _ in range(args.warmup):
-        run_oracle_sample(w, nsg_sample, 1)
+        oracle_sample(w, nsg_sample, 1, nt)
     vals, times = [], []
     for k in range(args.steps):
-        v, dt = run_oracle_sample(w, nsg_sample, 2 + k)
+        v, dt, _ = oracle_sample(w, nsg_sample, 2 + k, nt)
         vals.append(v)
         times.append(dt)
     val = float(np.mean(vals))
-    sample = "%s: 1 sample x %d supergather of %d shots, full %d steps, fwd+adj+imaging, FP64" % (
-        w.name, nsg_sample, w.sg_sizes[0], w.nt)
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -178,27 +195,36 @@ def reference_arm(args):
     return 0
 
 
-def native_arm(args):
-    import torch
-    import paper_2512_12797_gb300 as P
+def committed_traffic(kernel_name, ndim):
+    """DRAM bytes per wavefield point update of the named step kernel from the
+    committed ncu summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    src_name = "stencil3d.cu" if ndim == 3 else "stencil.cu"
+    prof = "step3d_layered3d_traffic.md" if ndim == 3 else "step2d_thrust2d_traffic.md"
+    try:
+        src = open(os.path.join(ROOT, "paper_2512_12797_gb300", "csrc", src_name), "rb").read()
+        txt = open(os.path.join(ROOT, "profiles", prof)).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic-key %s sha256=([0-9a-f]+) forward_bytes_per_update=([0-9.]+) "
+                  r"adjoint_bytes_per_update=([0-9.]+)" % re.escape(src_name), txt)
+    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    return float(m.group(3) if "ADJ" in kernel_name else m.group(2))
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    w = synth.WORKLOADS[args.workload](**({"nt": args.nt} if args.nt else {}))
-    if args.samples:
-        w.nsamp = args.samples
+
+def gradient_run(P, torch, w, steps, warmup, e2e_steps, dist, dev, world, rank, local, budget=0, variants="",
+                 clocks=True):
+    """Times `steps` full hot-path steps of workload w on device-resident inputs
+    (with per-phase events of the library), then `e2e_steps` through the public
+    API with host buffers.  Returns the pieces of the JSON line."""
     nsamp, sg = w.nsamp, w.sg_sizes
     nsg = len(sg)
     B = nsamp * nsg
-    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else 0
     ctx = P.FWI(w.grid_dict(), w.src, w.rec, B, budget)
-    if args.variants:
-        ctx.set_variants(*[int(x) for x in args.variants.split(",")])
+    if variants:
+        ctx.set_variants(*[int(x) for x in variants.split(",")])
 
     vel0 = synth.sample_models(w, nsamp, seed=100 + rank)
     d_obs_h = synth.random_records(w, 200 + rank)
@@ -207,8 +233,9 @@ def native_arm(args):
     xt = torch.zeros_like(vel)
     xprev = torch.zeros_like(vel)
     grad = torch.empty_like(vel)
+    mom = torch.zeros_like(vel)
     misfit = torch.empty(nsamp, dtype=torch.float64, device=dev)
-    sigma, eta = 1.0, 1e-3
+    sigma, eta = 1.0, 10.0
     beta = np.linspace(1e-4, 0.02, 1000)
     abar = np.cumprod(1 - beta)
     tlev = 300
@@ -220,7 +247,7 @@ def native_arm(args):
     def step(it, vel_d, dobs_d):
         perm, wt = encodings(it)
         ctx.gradient(vel_d, perm, wt, sg, dobs_d, sigma, grad=grad, misfit=misfit)
-        P.langevin_step(vel_d, grad, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it)
+        ctx.langevin_precond(vel_d, grad, mom, it + 1, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it, eps=0.1)
         P.renoise(xt, vel_d, abar[tlev - 1], abar[tlev - 2], beta[tlev - 1], 78, it, out=xprev)
 
     def barrier():
@@ -239,12 +266,11 @@ def native_arm(args):
             fn(it0 + k)
         ev1.record()
         barrier()
-        clocks = sampler.stop() if sampler else None
+        clk = sampler.stop() if sampler else None
         ms = max_over_ranks(ev0.elapsed_time(ev1) / nsteps, dist, dev)
-        return ms, clocks
+        return ms, clk
 
-    # warm-up
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k, vel, d_obs)
     torch.cuda.synchronize()
 
@@ -255,15 +281,14 @@ def native_arm(args):
 
     def step_prof(it):
         step(it, vel, d_obs)
-        ms, ln = ctx.phase_times()   # synchronises on the last phase event
-        phase_ms[:] += ms
+        ms_, ln = ctx.phase_times()   # synchronises on the last phase event
+        phase_ms[:] += ms_
         phase_launch[:] += ln
 
-    sampler = ClockSampler(local)
-    ms, clocks = timed(step_prof, args.steps, 1000, sampler)
+    ms, clk = timed(step_prof, steps, 1000, ClockSampler(local) if clocks else None)
     ctx.set_profiling(False)
     plan = ctx.plan_info()
-    variants = ctx.variants()
+    var = ctx.variants()
     units = 2.0 * w.padded_points * w.nt * B
     value = job_throughput(units, world, ms) / 1e9
 
@@ -280,7 +305,7 @@ def native_arm(args):
     cstream = torch.cuda.Stream()
     ready = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
-    e2e_range = {}
+    rng = {}
 
     def prefetch(it):
         b = it % 2
@@ -292,22 +317,21 @@ def native_arm(args):
 
     def step_e2e(it):
         b = it % 2
-        if it == e2e_range["first"]:
+        if it == rng["first"]:
             prefetch(it)
         torch.cuda.current_stream().wait_event(ready[b])
-        if it + 1 < e2e_range["end"]:
+        if it + 1 < rng["end"]:
             prefetch(it + 1)
         step(it, vel_e[b], dobs_e[b])
         out_h.copy_(vel_e[b], non_blocking=True)
         mis_h.copy_(misfit, non_blocking=True)
         free[b].record()
 
-    e2e_range.update(first=0, end=1)
+    rng.update(first=0, end=1)
     step_e2e(0)
     torch.cuda.synchronize()
-    n_e2e = max(1, args.steps)
-    e2e_range.update(first=2000, end=2000 + n_e2e)
-    ms_e2e, _ = timed(step_e2e, n_e2e, 2000)
+    rng.update(first=2000, end=2000 + e2e_steps)
+    ms_e2e, _ = timed(step_e2e, e2e_steps, 2000)
     e2e_value = job_throughput(units, world, ms_e2e) / 1e9
     h2d = vel_h.numel() * 4 + dobs_h.numel() * 4
     d2h = out_h.numel() * 4 + nsamp * 8
@@ -316,16 +340,15 @@ def native_arm(args):
     # launch runs all steps of a phase (forward: nt steps; adjoint: the steps of a
     # checkpoint segment), in 3D every step is a launch; both are charged per step.
     bpu = bytes_per_update(nsg, w.ndim)
-    n = args.steps
     nchunks = (nsamp + plan["samples_per_chunk"] - 1) // plan["samples_per_chunk"]
-    fwd_steps = w.nt * nchunks * n
-    rec_steps = plan["recomputed_steps"] * nchunks * n
+    fwd_steps = w.nt * nchunks * steps
+    rec_steps = plan["recomputed_steps"] * nchunks * steps
     fwd_step_ms = phase_ms[0] / max(fwd_steps, 1)  # phase 0 also holds one expand launch per chunk
     # the adjoint phase also holds the recomputed forward steps: charge them the
     # forward steps' average time
     adj_only_ms = phase_ms[2] - rec_steps * fwd_step_ms
-    adj_step_ms = adj_only_ms / max(w.nt * nchunks * n, 1)
-    per_step_pts = w.padded_points * plan["samples_per_chunk"] * nsg  # wavefields of one step
+    adj_step_ms = adj_only_ms / max(w.nt * nchunks * steps, 1)
+    per_step_pts = w.padded_points * plan["samples_per_chunk"] * nsg  # wavefield points of one step launch
     kd = "3d" if w.ndim == 3 else "2d"
     kern = {
         "step%s_kernel<ADJ>" % kd: {"ms": adj_step_ms, "bytes": bpu["adjoint"] * per_step_pts,
@@ -334,148 +357,102 @@ def native_arm(args):
                                     "share": (phase_ms[0] + phase_ms[2] - adj_only_ms) / max(phase_ms.sum(), 1e-9)},
     }
     dom = max(kern, key=lambda k: kern[k]["share"])
+    other = [k for k in kern if k != dom][0]
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = kern[dom]["bytes"] / (kern[dom]["ms"] * 1e-3) / 1e9
-    other = [k for k in kern if k != dom][0]
     other_gbs = kern[other]["bytes"] / (kern[other]["ms"] * 1e-3) / 1e9
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        cval, cdt = run_oracle_sample(w, 3, 3)
-        nthr = O.threads()
-        # the same oracle on one thread, over a shorter run (the rate per step
-        # does not depend on the number of steps)
-        w1 = synth.WORKLOADS[args.workload](nt=min(w.nt, 500))
-        O.threads(1)
-        try:
-            sval, sdt = run_oracle_sample(w1, 1, 4)
-        finally:
-            O.threads(nthr)
-        cpu = {"value": cval, "unit": UNIT, "cores": nthr, "kind": "oracle",
-               "sample": "%s: 1 sample x 3 supergathers of %d shots, full %d steps, fwd+adj+imaging, FP64 "
-                         "(%.1f s)" % (w.name, sg[0], w.nt, cdt),
-               "single_thread": {"value": sval, "unit": UNIT, "cores": 1,
-                                 "sample": "%s: 1 sample x 1 supergather of %d shots, first %d steps (%.1f s)"
-                                           % (w.name, w1.sg_sizes[0], w1.nt, sdt)}}
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded %s models, random records)" % w.name,
-           "config": {"workload": w.name, "grid": list(w.shape), "h_m": w.hx, "nb": w.nb, "nt": w.nt,
-                      "sources": w.ns, "receivers": w.nr, "samples": nsamp, "supergathers": sg,
-                      "wavefields_per_launch": B, "padded_points": w.padded_points,
-                      "parallelism": "replicas" if world > 1 else "single-gpu",
-                      "l2": "inputs larger than L2 (no flush)",
-                      "checkpoint_plan": plan,
-                      "step_kernels": {"forward": variants["forward_name"], "adjoint": variants["adjoint_name"],
-                                       "tuner_ms_forward": variants["forward_ms"],
-                                       "tuner_ms_adjoint": variants["adjoint_ms"]}},
+    tpu = committed_traffic(dom, w.ndim)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": tpu * per_step_pts if tpu is not None else None,
+                "traffic_unit": "bytes per launch (dram read + write per point update from ncu, profiles/%s, "
+                                "x the launch's point updates)" % ("step3d_layered3d_traffic.md" if w.ndim == 3
+                                                                   else "step2d_thrust2d_traffic.md"),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback",
+                "bytes_per_update": bpu["adjoint" if "ADJ" in dom else "forward"],
+                "point_updates_per_step": per_step_pts,
+                "avg_step_ms": kern[dom]["ms"],
+                "share_of_step": kern[dom]["share"],
+                "steps_per_launch": ({"forward": w.nt, "adjoint": min(plan["segment_len"], w.nt)}
+                                     if w.ndim == 2 else {"forward": 1, "adjoint": 1}),
+                "other_kernel": {"name": other, "achieved": other_gbs, "frac": other_gbs / peak,
+                                 "avg_step_ms": kern[other]["ms"], "share_of_step": kern[other]["share"]}}
+    res = {"value": value, "ms": ms, "clocks": clk, "units": units, "plan": plan, "variants": var,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "ms_per_step": ms_e2e,
+                   "ms_per_step": ms_e2e, "steps": e2e_steps,
                    "overlap": "double-buffered inputs: step k+1's H2D on a copy stream during step k"},
-           "gpu_launches": int(phase_launch.sum() + n * 2),
-           "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak,
-                        "traffic": (committed_traffic(dom) if w.name == "thrust2d" and nsamp == 16
-                                    and plan["samples_per_chunk"] == nsamp else None),
-                        "traffic_unit": "bytes per step (dram read + write, ncu, profiles/step2d_thrust2d_traffic.md)",
-                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
-                        "bytes_per_update": bpu["adjoint" if "ADJ" in dom else "forward"],
-                        "avg_step_ms": kern[dom]["ms"],
-                        "steps_per_launch": ({"forward": w.nt, "adjoint": min(plan["segment_len"], w.nt)}
-                                             if w.ndim == 2 else {"forward": 1, "adjoint": 1}),
-                        "other_kernel": {"name": other, "achieved": other_gbs, "frac": other_gbs / peak,
-                                         "avg_step_ms": kern[other]["ms"]}},
-           "phase_ms_per_step": {"forward": phase_ms[0] / n, "residual": phase_ms[1] / n,
-                                 "adjoint": phase_ms[2] / n, "finalize": phase_ms[3] / n},
-           "clocks": clocks, "cpu_baseline": cpu}
-
-    if args.sampler and world == 1:
-        # posterior samples/hr at the paper's schedule (300 refinement iterations
-        # per sample, Sec. 3.2): the encoded step timed above against one
-        # full-shot Langevin step (every shot its own supergather, weight +1)
-        ident = np.arange(w.ns, dtype=np.int32)
-        ones = np.ones(w.ns, np.int8)
-        full_sg = [1] * w.ns
-        ctx.close()
-        torch.cuda.synchronize()
-        ctxf = P.FWI(w.grid_dict(), w.src, w.rec, nsamp * w.ns, 0)
-
-        def step_full(it):
-            ctxf.gradient(vel, ident, ones, full_sg, d_obs, sigma, scale=1.0, grad=grad, misfit=misfit)
-            ctxf.smooth_prior_grad(vel, vel[0].contiguous(), 10.0, 0.0, grad)
-            P.langevin_step(vel, grad, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it)
-
-        step_full(0)
-        ms_full, _ = timed(step_full, 1, 4000)
-        iters = 300
-        enc_solves = 2 * nsg * iters
-        full_solves = 2 * w.ns * iters
-        out["sampler"] = {
-            "schedule": "300 refinement iterations per posterior sample (Sec. 3.2), %d samples per batch" % nsamp,
-            "encoded": {"ms_per_iteration": ms, "samples_per_hour": nsamp * 3600e3 / (ms * iters),
-                        "pde_solves_per_sample": enc_solves, "supergathers": sg},
-            "plain_langevin_full_shot": {"ms_per_iteration": ms_full,
-                                         "samples_per_hour": nsamp * 3600e3 / (ms_full * iters),
-                                         "pde_solves_per_sample": full_solves,
-                                         "samples_per_chunk": ctxf.plan_info()["samples_per_chunk"]},
-            "speedup": ms_full / ms,
-            "note": "equal iteration counts; on the small 2D case encoded Langevin reached the full-shot RMSE "
-                    "with 4x the iterations at half the solves (tests/test_gpu_sampler.py)"}
-        ctxf.close()
-        ctx = None
-    if args.checkpointed and world == 1:
-        # same step with a workspace that forces checkpointing and recompute
-        if ctx is not None:
-            ctx.close()
-        torch.cuda.synchronize()
-        ctx2 = P.FWI(w.grid_dict(), w.src, w.rec, B, int(args.checkpointed * (1 << 30)))
-        ctx_saved = ctx2
-
-        def step_ck(it):
-            perm, wt = encodings(it)
-            ctx_saved.gradient(vel, perm, wt, sg, d_obs, sigma, grad=grad, misfit=misfit)
-            P.langevin_step(vel, grad, eta, (2 * eta) ** 0.5, w.vmin, w.vmax, 77, it)
-            P.renoise(xt, vel, abar[tlev - 1], abar[tlev - 2], beta[tlev - 1], 78, it, out=xprev)
-
-        step_ck(0)
-        ms_ck, _ = timed(step_ck, 2, 3000)
-        out["checkpointed"] = {"value": units / (ms_ck * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_ck,
-                               "budget_gb": args.checkpointed, "plan": ctx2.plan_info()}
-    if args.prior and world == 1 and w.ndim == 2:
-        out["prior"] = prior_measurement(w, nsamp, ms, peaks)
-    if rank == 0:
-        print(json.dumps(out))
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+           # library launches counted per phase, plus the two refinement-step
+           # kernels and the re-noise kernel of every step
+           "gpu_launches": int(phase_launch.sum() + steps * 3),
+           "roofline": roofline,
+           "phase_ms_per_step": {"forward": phase_ms[0] / steps, "residual": phase_ms[1] / steps,
+                                 "adjoint": phase_ms[2] / steps, "finalize": phase_ms[3] / steps}}
+    ctx.close()
+    del vel_e, dobs_e, vel, d_obs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
 
 
-def committed_traffic(kernel_name):
-    """DRAM bytes per step of the named step kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    import hashlib
-    import re
-    here = os.path.dirname(os.path.abspath(__file__))
-    try:
-        src = open(os.path.join(here, "paper_2512_12797_gb300", "csrc", "stencil.cu"), "rb").read()
-        txt = open(os.path.join(here, "profiles", "step2d_thrust2d_traffic.md")).read()
-    except OSError:
-        return None
-    m = re.search(r"traffic-key stencil.cu sha256=([0-9a-f]+) forward_bytes_per_step=(\d+) "
-                  r"adjoint_bytes_per_step=(\d+)", txt)
-    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
-        return None
-    return float(m.group(3) if "ADJ" in kernel_name else m.group(2))
+def sampler_at_equal_rmse(P, torch, dev, full_steps=6, max_enc_steps=120):
+    """Posterior samples/hour at equal model RMSE (Sec. 2.4, eq. pde-count; the
+    encoded sampler against plain full-shot Langevin) on the thrust-belt
+    geometry: 4 posterior samples, observed data from the forward on the
+    seeded truth plus 1 % Gaussian noise.  The full-shot chain (every shot
+    its own solve) runs full_steps preconditioned Langevin steps; its final
+    posterior-mean RMSE is the target; the encoded chain (5 supergathers of
+    20, redrawn every step) runs until it reaches that RMSE."""
+    from paper_2512_12797_gb300 import sampler as S
+    w = synth.thrust2d()
+    nsamp = 4
+    ctx = P.FWI(w.grid_dict(), w.src, w.rec, nsamp * w.ns, 0)
+    truth = torch.tensor(synth.true_model(w), device=dev)
+    v0 = torch.tensor(synth.sample_models(w, nsamp, seed=7), device=dev)
+    ident = np.arange(w.ns, dtype=np.int32)
+    d_clean = ctx.forward(truth[None].contiguous(), ident, np.ones(w.ns, np.int8), [1] * w.ns)[0]
+    gen = torch.Generator(device=dev).manual_seed(4)
+    noise = 0.01 * float(d_clean.pow(2).mean().sqrt())
+    d_obs = (d_clean + noise * torch.randn(d_clean.shape, device=dev, generator=gen)).contiguous()
+    kw = dict(eta=15.0, vmin=w.vmin, vmax=w.vmax, sigma=noise, seed=3)
+    # untimed first calls (autotuner, plans) of both shapes
+    S.plain_langevin(ctx, v0, d_obs, truth, steps=1, **kw)
+    S.plain_langevin(ctx, v0, d_obs, truth, steps=1, sg_sizes=w.sg_sizes, **kw)
+    full = S.plain_langevin(ctx, v0, d_obs, truth, steps=full_steps, **kw)
+    target = full["rmse"][-1]
+    enc = S.plain_langevin(ctx, v0, d_obs, truth, steps=max_enc_steps, sg_sizes=w.sg_sizes, rmse_target=target, **kw)
+    ctx.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    def arm(solves, seconds, steps, per_step):
+        return {"solves_to_target": solves, "seconds_to_target": seconds, "steps_to_target": steps,
+                "pde_solves_per_step_per_sample": per_step,
+                "samples_per_hour_at_target": nsamp * 3600.0 / seconds if seconds else None}
+
+    out = {"workload": "thrust2d geometry, %d posterior samples, 1 %% noise, preconditioned Langevin with matched "
+                       "noise (eta 15 m/s)" % nsamp,
+           "rmse_initial": full["rmse"][0], "rmse_target": target,
+           "plain_langevin_full_shot": arm(full["solves"][-1], full["seconds"], full_steps, 2 * w.ns),
+           "encoded": None, "samples_per_hour_ratio": None, "solve_ratio": None}
+    if enc["reached"] is not None:
+        r = enc["reached"]
+        out["encoded"] = arm(r["solves"], r["seconds"], r["steps"], 2 * len(w.sg_sizes))
+        out["samples_per_hour_ratio"] = (out["encoded"]["samples_per_hour_at_target"] /
+                                         out["plain_langevin_full_shot"]["samples_per_hour_at_target"])
+        out["solve_ratio"] = full["solves"][-1] / r["solves"]
+    else:
+        out["encoded_final_rmse"] = enc["rmse"][-1]
+        out["encoded_steps_run"] = max_enc_steps
+    return out
 
 
 def prior_measurement(w, nsamp, ms_iter, peaks):
     """The learned prior's x0-hat prediction on this batch's models, on the
     tcgen05 kernels: time per call, the convolutions' algorithmic TFLOP/s
-    against the measured BF16 peak, and its cost next to one encoded Langevin
-    iteration.  (Random weights: the arithmetic does not depend on them.)"""
+    (real input channels, not the zero-padded ones) against the measured BF16
+    peak, and its cost next to one encoded Langevin iteration.  (Random
+    weights: the arithmetic does not depend on them.)"""
     import torch
     from paper_2512_12797_gb300 import unet
     den = unet.UNetDenoiser(unet.init_params(0, out_scale=1.0))
@@ -483,7 +460,7 @@ def prior_measurement(w, nsamp, ms_iter, peaks):
     flops = 0.0
     for name, cin, cout in unet.LAYERS:
         lev = {"e1": 0, "e2": 1, "ba": 2, "bb": 2, "d2": 1, "d1": 0}[name[:2]]
-        flops += 2.0 * (Hp >> lev) * (Wp >> lev) * 9 * ((cin + 63) // 64 * 64) * cout
+        flops += 2.0 * (Hp >> lev) * (Wp >> lev) * 9 * cin * cout
     flops = (flops + 2.0 * Hp * Wp * 64 * 32) * nsamp
     x_t = torch.randn((nsamp, w.nz, w.nx), device="cuda")
     for _ in range(3):
@@ -503,7 +480,86 @@ def prior_measurement(w, nsamp, ms_iter, peaks):
             "conv_tflops": flops / (ms * 1e-3) / 1e12, "bf16_peak_tflops": peak,
             "frac_of_peak": flops / (ms * 1e-3) / 1e12 / peak,
             "share_of_langevin_iteration": ms / ms_iter,
-            "note": "whole call incl. padding, pooling, upsampling and concatenation (PyTorch tensor ops)"}
+            "note": "whole call incl. padding, pooling, upsampling and concatenation; FLOPs of the real channels"}
+
+
+def native_arm(args):
+    import torch
+    import paper_2512_12797_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload](**({"nt": args.nt} if args.nt else {}))
+    if args.samples:
+        w.nsamp = args.samples
+    budget = int(args.budget_gb * (1 << 30)) if args.budget_gb else 0
+    e2e_steps = args.e2e_steps or (args.steps if w.ndim == 2 else max(3, args.steps // 4))
+    r = gradient_run(P, torch, w, args.steps, args.warmup, e2e_steps, dist, dev, world, rank, local, budget,
+                     args.variants)
+    nsg = len(w.sg_sizes)
+    B = w.nsamp * nsg
+    peaks = _peaks()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        nsg_s, nt_s, sample = _oracle_sample_plan(w)
+        cval, cdt, _ = oracle_sample(w, nsg_s, 3, nt_s)
+        nthr = O.threads()
+        # the same oracle on one thread, over a shorter run (the rate per step
+        # does not depend on the number of steps)
+        O.threads(1)
+        try:
+            sval, sdt, w1 = oracle_sample(w, 1, 4, min(w.nt, 500 if w.ndim == 2 else 8))
+        finally:
+            O.threads(nthr)
+        cpu = {"value": cval, "unit": UNIT, "cores": nthr, "kind": "oracle", "sample": sample + " (%.1f s)" % cdt,
+               "single_thread": {"value": sval, "unit": UNIT, "cores": 1,
+                                 "sample": "%s: 1 sample x 1 supergather of %d shots, first %d steps (%.1f s)"
+                                           % (w.name, w1.sg_sizes[0], w1.nt, sdt)}}
+
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded %s models, random records)" % w.name,
+           "config": {"workload": w.name, "grid": list(w.shape), "h_m": w.hx, "nb": w.nb, "nt": w.nt,
+                      "sources": w.ns, "receivers": w.nr, "samples": w.nsamp, "supergathers": w.sg_sizes,
+                      "wavefields": B, "padded_points": w.padded_points,
+                      "parallelism": "replicas" if world > 1 else "single-gpu",
+                      "l2": "inputs larger than L2 (no flush)",
+                      "checkpoint_plan": r["plan"],
+                      "step_kernels": {"forward": r["variants"]["forward_name"],
+                                       "adjoint": r["variants"]["adjoint_name"],
+                                       "tuner_ms_forward": r["variants"]["forward_ms"],
+                                       "tuner_ms_adjoint": r["variants"]["adjoint_ms"]}},
+           "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "roofline": r["roofline"],
+           "phase_ms_per_step": r["phase_ms_per_step"], "clocks": r["clocks"], "cpu_baseline": cpu}
+
+    if world == 1 and args.extras and w.name != "thrust2d" and not args.nt and not args.samples:
+        # the 2D thrust-belt batch: its own line's figures, fewer steps
+        w2 = synth.thrust2d()
+        r2 = gradient_run(P, torch, w2, args.extra_steps, 2, args.extra_steps, None, dev, 1, 0, local, clocks=False)
+        out["thrust2d"] = {"value": r2["value"], "unit": UNIT, "ms_per_step": r2["ms"], "steps": args.extra_steps,
+                           "config": {"grid": list(w2.shape), "nt": w2.nt, "samples": w2.nsamp,
+                                      "supergathers": w2.sg_sizes, "plan": r2["plan"]},
+                           "e2e": r2["e2e"], "roofline": r2["roofline"], "phase_ms_per_step": r2["phase_ms_per_step"],
+                           "gpu_launches": r2["gpu_launches"]}
+        ms2 = r2["ms"]
+    else:
+        w2, ms2 = (w, r["ms"]) if w.ndim == 2 else (None, None)
+    if world == 1 and args.sampler:
+        out["sampler"] = sampler_at_equal_rmse(P, torch, dev)
+    if world == 1 and args.prior and w2 is not None:
+        out["prior"] = prior_measurement(w2, w2.nsamp, ms2, peaks)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
 
 
 def main():
@@ -514,10 +570,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--budget-gb", type=float, default=0.0, help="wavefield pool (0: most of free memory)")
-    ap.add_argument("--checkpointed", type=float, default=16.0,
-                    help="also time the step with a pool of this many GB (forces recompute); 0 disables")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end timing (0: automatic)")
+    ap.add_argument("--extras", type=int, default=1, help="also time the 2D thrust-belt batch")
+    ap.add_argument("--extra-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sampler", type=int, default=1, help="also time one full-shot Langevin step (samples/hr)")
+    ap.add_argument("--sampler", type=int, default=1, help="also measure posterior samples/hr at equal RMSE")
     ap.add_argument("--prior", type=int, default=1, help="also time the learned prior's x0-hat prediction")
     ap.add_argument("--samples", type=int, default=0, help="override posterior samples (profiling runs)")
     ap.add_argument("--nt", type=int, default=0, help="override time steps (profiling runs)")

@@ -179,6 +179,39 @@ int langevin_step(float* z, const float* grad, int64_t n, double eta, double nu,
                   double vmax, uint64_t seed, uint64_t counter, void* stream);
 
 /*
+ * Preconditioned clean-space Langevin step (Sec. 2.3 (ii) with a diagonal
+ * preconditioner; Sec. 5 requires the noise to be matched to any
+ * preconditioning, and Sec. 3.2 refines with Adam).  For each sample s of
+ * nsamp, over its phys = nz*ny*nx elements i (layout [nsamp][phys], float32,
+ * device), at step number k >= 1 (k = 0: no bias correction):
+ *   v_i <- alpha v_i + (1 - alpha) g_i^2                     (second moment, in/out)
+ *   m_i <- beta1 m_i + (1 - beta1) g_i                       (first moment, in/out; only if m != NULL)
+ *   vh_i = v_i / (1 - alpha^k),  mh_i = m_i / (1 - beta1^k)
+ *   r_s  = sqrt(mean_i vh_i)                                  (per-sample scale)
+ *   G_i  = 1 / (sqrt(vh_i) + eps r_s)                        (0 where the denominator is 0)
+ *   d_i  = mh_i if m != NULL else g_i
+ *   z_i <- clamp(z_i - eta G_i d_i + nu sqrt(G_i) xi_i, vmin, vmax)
+ * xi_i is normal number s*phys + i of stream (seed, counter), as in
+ * langevin_step.  With m == NULL and nu = sqrt(2 eta) this is preconditioned
+ * SGLD (Li et al. 2016): eta is a step in model units (m/s) and the injected
+ * noise has the variance the preconditioner implies; another nu scales the
+ * noise independently (Sec. 2.3 closing paragraph).  With m != NULL and nu = 0
+ * it is an Adam step (the deterministic refinement, Sec. 3.2).
+ *   z, v, m device [nsamp][phys] float32, owned by the caller; v and m hold
+ *           the moments between calls (start them at zero)
+ *   grad    device [nsamp][phys] float32 (read only)
+ * Two launches on `stream`: the moments with per-block FP64 partial sums of
+ * vh into the context's reduction buffer (deterministic order), then the
+ * update.  Calls on one context share that buffer with fwi_gradient: issue
+ * them on one stream.  FWI_ERR_ARG: null pointer, nsamp outside
+ * [1, max_wavefields], alpha outside [0, 1], beta1 outside [0, 1) when m is
+ * given, negative eps/eta/nu, vmin > vmax, or alpha = 1 with k > 0.
+ */
+int langevin_step_precond(fwi_ctx* ctx, float* z, const float* grad, float* v, float* m, int nsamp,
+                          double alpha, double beta1, double eps, int64_t k, double eta, double nu,
+                          double vmin, double vmax, uint64_t seed, uint64_t counter, void* stream);
+
+/*
  * DDPM re-noise to the next level (Sec. 2.3 (iii), DDPM posterior mean and
  * variance), elementwise on n float32 device values:
  *   x_prev = sqrt(abar_prev) beta_t/(1-abar_t) x0 + sqrt(1-beta_t)(1-abar_prev)/(1-abar_t) x_t

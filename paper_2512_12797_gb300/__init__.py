@@ -163,6 +163,27 @@ class FWI:
                                       _stream(stream)), "smooth_prior_grad")
         return grad
 
+    def langevin_precond(self, z, grad, v, k, eta, nu, vmin, vmax, seed, counter, m=None, alpha=0.9, beta1=0.9,
+                         eps=1e-2, stream=None):
+        """In place: preconditioned Langevin (m None) or Adam (m given, nu 0)
+        step on z [nsamp, *shape], moments v (and m) updated; k >= 1 is the
+        step number of the bias correction (langevin_step_precond)."""
+        torch = _torch()
+        nsamp = z.shape[0]
+        n = nsamp * self.phys
+        _numel(z, n, "z")
+        _numel(grad, n, "grad")
+        _numel(v, n, "v")
+        if m is not None:
+            _numel(m, n, "m")
+        check(lib().langevin_step_precond(self._h, _dev_ptr(z, torch.float32, "z"), _dev_ptr(grad, torch.float32, "grad"),
+                                          _dev_ptr(v, torch.float32, "v"),
+                                          _dev_ptr(m, torch.float32, "m") if m is not None else None, nsamp,
+                                          float(alpha), float(beta1), float(eps), int(k), float(eta), float(nu),
+                                          float(vmin), float(vmax), ctypes.c_uint64(seed), ctypes.c_uint64(counter),
+                                          _stream(stream)), "langevin_step_precond")
+        return z
+
     def plan_info(self):
         K, S, used, avail = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         rec = ctypes.c_int64()
@@ -203,6 +224,7 @@ class FWI:
 def langevin_step(z, grad, eta, nu, vmin, vmax, seed, counter, stream=None):
     """In place: z <- clamp(z - eta grad + nu xi, vmin, vmax) (langevin_step)."""
     torch = _torch()
+    _numel(grad, z.numel(), "grad")
     check(lib().langevin_step(_dev_ptr(z, torch.float32, "z"), _dev_ptr(grad, torch.float32, "grad"), z.numel(),
                               float(eta), float(nu), float(vmin), float(vmax), ctypes.c_uint64(seed),
                               ctypes.c_uint64(counter), _stream(stream)), "langevin_step")
@@ -214,6 +236,8 @@ def renoise(x_t, x0, abar_t, abar_prev, beta_t, seed, counter, out=None, stream=
     torch = _torch()
     if out is None:
         out = torch.empty_like(x_t)
+    _numel(x0, x_t.numel(), "x0")
+    _numel(out, x_t.numel(), "out")
     check(lib().renoise(_dev_ptr(out, torch.float32, "out"), _dev_ptr(x_t, torch.float32, "x_t"),
                         _dev_ptr(x0, torch.float32, "x0"), x_t.numel(), float(abar_t), float(abar_prev), float(beta_t),
                         ctypes.c_uint64(seed), ctypes.c_uint64(counter), _stream(stream)), "renoise")

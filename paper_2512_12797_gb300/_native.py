@@ -14,7 +14,7 @@ FWI_STATUS = {0: "FWI_OK", -1: "FWI_ERR_ARG", -2: "FWI_ERR_CFL", -3: "FWI_ERR_OO
 
 # every symbol fwi.h declares
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradient", "fwi_adjoint", "langevin_step",
-           "renoise",
+           "langevin_step_precond", "renoise",
            "smooth_prior_grad", "fwi_status_string", "fwi_last_device_status", "fwi_plan_info",
            "fwi_set_profiling", "fwi_phase_times", "fwi_residual_misfit_noalloc", "fwi_last_cuda_error",
            "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking", "fwi_checkpoint_schedule"]
@@ -62,6 +62,9 @@ _SIGS = {
     "fwi_adjoint": (ctypes.c_int, [_P, _P, ctypes.c_int, _I32P, _I8P, _I32P, ctypes.c_int, _P, _P, _P]),
     "langevin_step": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, _P]),
+    "langevin_step_precond": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, _P]),
     "renoise": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_uint64, ctypes.c_uint64, _P]),
     "smooth_prior_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P]),

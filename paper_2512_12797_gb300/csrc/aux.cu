@@ -271,6 +271,85 @@ cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, d
   return cudaGetLastError();
 }
 
+// Preconditioned Langevin step, pass 1: running moments per element
+//   v <- alpha v + (1 - alpha) g^2,   m <- beta1 m + (1 - beta1) g   (m optional)
+// and per-block FP64 partial sums of the bias-corrected second moment
+// vh = v * inv_cv of each sample (blockIdx.y), over the values as stored in
+// FP32 so that pass 2 sees the same numbers; fixed reduction order.
+__global__ void precond_moments_kernel(const float* __restrict__ g, float* __restrict__ v, float* __restrict__ m,
+                                       long long per, double alpha, double beta1, double inv_cv, double* part,
+                                       int nblk) {
+  const int s = blockIdx.y;
+  const long long o = (long long)s * per;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)gridDim.x * blockDim.x) {
+    const double gi = (double)g[o + i];
+    const float vn = (float)(alpha * (double)v[o + i] + (1.0 - alpha) * gi * gi);
+    v[o + i] = vn;
+    if (m) m[o + i] = (float)(beta1 * (double)m[o + i] + (1.0 - beta1) * gi);
+    acc += (double)vn * inv_cv;
+  }
+  __shared__ double sh[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[(long long)s * nblk + blockIdx.x] = t;
+  }
+}
+
+// Pass 2: r = sqrt(mean vh) of the sample (its nblk partials summed in a
+// fixed order), G = 1/(sqrt(vh) + eps r) (0 where that is 0), drift d = g or
+// the bias-corrected first moment, and
+//   z <- clamp(z - eta G d + nu sqrt(G) xi, vmin, vmax),
+// xi number s * per + i of the counter-based normal stream.
+__global__ void precond_update_kernel(float* z, const float* __restrict__ g, const float* __restrict__ v,
+                                      const float* __restrict__ m, long long per, const double* __restrict__ part,
+                                      int nblk, double inv_cv, double inv_cm, double eps, double eta, double nu,
+                                      double vmin, double vmax, uint64_t key) {
+  const int s = blockIdx.y;
+  const long long o = (long long)s * per;
+  __shared__ double r_sh;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) t += part[(long long)s * nblk + b];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) r_sh = sqrt(t / (double)per);
+  }
+  __syncthreads();
+  const double er = eps * r_sh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)gridDim.x * blockDim.x) {
+    const double den = sqrt((double)v[o + i] * inv_cv) + er;
+    const double G = den > 0.0 ? 1.0 / den : 0.0;
+    const double d = m ? (double)m[o + i] * inv_cm : (double)g[o + i];
+    double x = (double)z[o + i] - eta * G * d;
+    if (nu != 0.0) x += nu * sqrt(G) * normal_at(key, (uint64_t)(o + i));
+    z[o + i] = (float)fmin(fmax(x, vmin), vmax);
+  }
+}
+
+cudaError_t launch_langevin_precond(float* z, const float* g, float* v, float* m, int nsamp, long long per,
+                                    double alpha, double beta1, double eps, long long k, double eta, double nu,
+                                    double vmin, double vmax, uint64_t seed, uint64_t counter, double* part,
+                                    int nblk, cudaStream_t st) {
+  const double cv = k > 0 ? 1.0 - pow(alpha, (double)k) : 1.0;
+  const double cm = k > 0 ? 1.0 - pow(beta1, (double)k) : 1.0;
+  auto mx = [](uint64_t x) {
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    return x ^ (x >> 31);
+  };
+  const uint64_t key = mx(seed ^ mx(counter));
+  const int per_blocks = grid_for(per, 16);
+  precond_moments_kernel<<<dim3(nblk, nsamp), 256, 0, st>>>(g, v, m, per, alpha, beta1, 1.0 / cv, part, nblk);
+  const int ub = (per_blocks + nsamp - 1) / nsamp > 0 ? (per_blocks + nsamp - 1) / nsamp : 1;
+  precond_update_kernel<<<dim3(ub, nsamp), 256, 0, st>>>(z, g, v, m, per, part, nblk, 1.0 / cv, 1.0 / cm, eps,
+                                                         eta, nu, vmin, vmax, key);
+  return cudaGetLastError();
+}
+
 __global__ void renoise_kernel(float* xp, const float* __restrict__ xt, const float* __restrict__ x0, long long n,
                                double c0, double ct, double sd, uint64_t key) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {

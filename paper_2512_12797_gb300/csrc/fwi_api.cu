@@ -1148,6 +1148,19 @@ int langevin_step(float* z, const float* grad, int64_t n, double eta, double nu,
   return FWI_OK;
 }
 
+int langevin_step_precond(fwi_ctx* C, float* z, const float* grad, float* v, float* m, int nsamp, double alpha,
+                          double beta1, double eps, int64_t k, double eta, double nu, double vmin, double vmax,
+                          uint64_t seed, uint64_t counter, void* stream) {
+  if (!C || !z || !grad || !v || nsamp < 1 || nsamp > C->max_B || k < 0) return FWI_ERR_ARG;
+  if (!(alpha >= 0 && alpha <= 1) || !(eps >= 0) || !(eta >= 0) || !(nu >= 0) || !(vmin <= vmax))
+    return FWI_ERR_ARG;
+  if (m && !(beta1 >= 0 && beta1 < 1)) return FWI_ERR_ARG;
+  if (k > 0 && !(1.0 - pow(alpha, (double)k) > 0)) return FWI_ERR_ARG;  // alpha = 1 needs k = 0
+  CK(launch_langevin_precond(z, grad, v, m, nsamp, C->L.phys, alpha, beta1, eps, k, eta, nu, vmin, vmax, seed,
+                             counter, C->part, C->nblk, (cudaStream_t)stream));
+  return FWI_OK;
+}
+
 int renoise(float* x_prev, const float* x_t, const float* x0, int64_t n, double abar_t, double abar_prev,
             double beta_t, uint64_t seed, uint64_t counter, void* stream) {
   if (!x_prev || !x_t || !x0 || n < 0) return FWI_ERR_ARG;

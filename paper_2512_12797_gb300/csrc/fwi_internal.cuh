@@ -112,6 +112,10 @@ cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, i
 cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, double nu,
                             double vmin, double vmax, uint64_t seed, uint64_t counter,
                             cudaStream_t st);
+cudaError_t launch_langevin_precond(float* z, const float* g, float* v, float* m, int nsamp, long long per,
+                                    double alpha, double beta1, double eps, long long k, double eta, double nu,
+                                    double vmin, double vmax, uint64_t seed, uint64_t counter, double* part,
+                                    int nblk, cudaStream_t st);
 cudaError_t launch_renoise(float* xp, const float* xt, const float* x0, long long n, double c0,
                            double ct, double sd, uint64_t seed, uint64_t counter, cudaStream_t st);
 cudaError_t launch_prior(const Layout& L, const float* z, const float* zref, int nsamp,

@@ -9,13 +9,20 @@ encoded_diffusion_sampler -- the decoupled, encoded-shot sampler of Sec. 2.3:
 plain_langevin -- the baseline: unadjusted Langevin on the full-shot
     likelihood (every shot its own solve) plus a Gaussian smoothness prior.
 
-Both use the same Langevin kernel and the same reading of the step size "in
-physical units" (Sec. 2.3 (ii)): the gradient term is preconditioned per
-element by the running root-mean-square of that element's gradient (the
-diagonal preconditioner of preconditioned SGLD, Li et al. 2016, the Langevin
-counterpart of the Adam refinement of Sec. 3.2), so each step moves an
-element by about eta m/s; the independent noise has standard deviation nu
-m/s.
+Both use the same refinement kernel (langevin_step_precond) with the
+paper's requirement that the noise be matched to any preconditioning
+(Sec. 5): the drift is preconditioned per element by the running
+root-mean-square of that element's gradient (RMSprop second moment, the
+diagonal preconditioner G of preconditioned SGLD, Li et al. 2016), and the
+injected noise is nu sqrt(G) xi with nu = sqrt(2 eta) by default, so the
+chain targets the tempered posterior of Sec. 2.3 up to the step's O(eta)
+bias.  eta is a step in m/s ("physical units", Sec. 2.3 (ii)): a step
+moves a well-informed element by about eta.  The preconditioner's damping
+eps is relative to each sample's gradient scale.  A different nu is the
+paper's independent noise scale (Sec. 2.3, closing paragraph).  The
+deterministic variant (refine="adam") runs Adam through the same kernel
+with nu = 0.  Every update runs in the library: no PyTorch arithmetic sits
+between the gradient and the step.
 
 The clean-model predictor is any callable (x_t, abar_t) -> x0^: the learned
 network g_theta of Sec. 2.2 (unet.UNetDenoiser, unet3d.UNet3DDenoiser on the
@@ -35,7 +42,7 @@ import time
 
 import numpy as np
 
-from . import encode, langevin_step, renoise
+from . import encode, renoise
 
 
 def ddpm_schedule(T=1000, beta1=1e-4, betaT=0.02):
@@ -87,61 +94,39 @@ def _rmse(v, truth):
     return float(((v - truth) ** 2).mean().sqrt())
 
 
-def _rms_normalise(grad):
-    """Divide each sample's gradient by its root-mean-square value (in place)."""
-    g = grad.reshape(grad.shape[0], -1)
-    g.div_(g.pow(2).mean(dim=1).sqrt().clamp_min(1e-30)[:, None])
+class Moments:
+    """Moment buffers of the refinement kernel: the second moment v (and, for
+    Adam, the first moment m) per element, plus the step count k of the bias
+    correction.  Plain tensors, so a sampler state can be saved and resumed."""
 
-
-class RMSPreconditioner:
-    """Diagonal preconditioner of preconditioned SGLD: g -> g / (sqrt(v) + eps),
-    v the exponential moving average of g^2 per element (in place on g)."""
-
-    def __init__(self, like, alpha=0.9, eps=1e-3):
+    def __init__(self, like, adam=False):
         import torch
         self.v = torch.zeros_like(like)
-        self.alpha, self.eps, self.n = alpha, eps, 0
+        self.m = torch.zeros_like(like) if adam else None
+        self.k = 0
 
     def state_dict(self):
-        return {"v": self.v.clone(), "n": self.n}
+        st = {"v": self.v.clone(), "k": self.k}
+        if self.m is not None:
+            st["m"] = self.m.clone()
+        return st
 
     def load_state_dict(self, st):
         self.v.copy_(st["v"])
-        self.n = int(st["n"])
-
-    def __call__(self, g):
-        self.n += 1
-        self.v.mul_(self.alpha).addcmul_(g, g, value=1.0 - self.alpha)
-        vhat = self.v / (1.0 - self.alpha ** self.n)
-        g.div_(vhat.sqrt().add_(self.eps))
+        if self.m is not None:
+            self.m.copy_(st["m"])
+        self.k = int(st["k"])
 
 
-class AdamState:
-    """Adam moments (Kingma & Ba 2015) for the deterministic refinement variant
-    (A15): g -> m-hat / (sqrt(v-hat) + eps) in place, m and v the exponential
-    moving averages of g and g^2 (beta1 0.9, beta2 0.999)."""
-
-    def __init__(self, like, beta1=0.9, beta2=0.999, eps=1e-8):
-        import torch
-        self.m = torch.zeros_like(like)
-        self.v = torch.zeros_like(like)
-        self.b1, self.b2, self.eps, self.n = beta1, beta2, eps, 0
-
-    def state_dict(self):
-        return {"m": self.m.clone(), "v": self.v.clone(), "n": self.n}
-
-    def load_state_dict(self, st):
-        self.m.copy_(st["m"])
-        self.v.copy_(st["v"])
-        self.n = int(st["n"])
-
-    def __call__(self, g):
-        self.n += 1
-        self.m.mul_(self.b1).add_(g, alpha=1.0 - self.b1)
-        self.v.mul_(self.b2).addcmul_(g, g, value=1.0 - self.b2)
-        mhat = self.m / (1.0 - self.b1 ** self.n)
-        vhat = self.v / (1.0 - self.b2 ** self.n)
-        g.copy_(mhat / (vhat.sqrt() + self.eps))
+def refine_step(ctx, z, grad, mom, eta, nu, vmin, vmax, seed, counter, eps=0.1, adam=False):
+    """One refinement step in place on z (langevin_step_precond): the
+    preconditioned Langevin step with matched noise, or with adam=True an
+    Adam step (beta1 0.9, beta2 0.999, no noise)."""
+    mom.k += 1
+    if adam:
+        return ctx.langevin_precond(z, grad, mom.v, mom.k, eta, 0.0, vmin, vmax, seed, counter, m=mom.m, alpha=0.999,
+                                    beta1=0.9, eps=eps)
+    return ctx.langevin_precond(z, grad, mom.v, mom.k, eta, nu, vmin, vmax, seed, counter, alpha=0.9, eps=eps)
 
 
 def _sync(t):
@@ -150,18 +135,22 @@ def _sync(t):
         torch.cuda.synchronize(t.device)
 
 
-def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, prior_lam=0.0, prior_mu=0.0,
-                   zref=None, seed=0, record_every=1, sg_sizes=None):
-    """Unadjusted Langevin on the full-shot likelihood (+ smoothness prior).
+def plain_langevin(ctx, v0, d_obs, truth, steps, eta, vmin, vmax, sigma, nu=None, prior_lam=0.0, prior_mu=0.0,
+                   zref=None, seed=0, record_every=1, sg_sizes=None, eps=0.1, rmse_target=None):
+    """Preconditioned Langevin on the full-shot likelihood (+ smoothness prior).
 
     Every gradient evaluation solves each shot separately (N_s supergathers
     of one shot, weight +1) -- or, with sg_sizes, uses the unbiased encoded
     gradient of supergathers of those sizes, redrawn every step (Sec. 2.1,
-    3.2).  The RMS-normalised data gradient is combined with the gradient of
-    the smoothness prior lam/2 |grad(z - zref)|^2 + mu/2 |z - zref|^2.
-    Returns dict(rmse=[...], solves=[...], seconds, samples).
+    3.2).  The data gradient plus the gradient of the smoothness prior
+    lam/2 |grad(z - zref)|^2 + mu/2 |z - zref|^2 drives the preconditioned
+    Langevin step (nu None: sqrt(2 eta), the posterior-targeting noise).
+    With rmse_target the run stops at the first recorded posterior-mean RMSE
+    at or below it.  Returns dict(rmse=[...], solves=[...], seconds, samples,
+    reached: solves and seconds when the target was first met, else None).
     """
     import torch
+    nu = math.sqrt(2.0 * eta) if nu is None else nu
     z = v0.clone()
     ns = ctx.ns
     nsamp = z.shape[0]
@@ -173,37 +162,43 @@ def plain_langevin(ctx, v0, d_obs, truth, steps, eta, nu, vmin, vmax, sigma, pri
     else:
         sg = list(sg_sizes)
     hist_r, hist_s = [_rmse(z.mean(0), truth)], [0]
-    zref = v0.mean(0) if zref is None else zref
+    zref = (v0.mean(0) if zref is None else zref).contiguous()
     grad = torch.empty_like(z)
-    precond = RMSPreconditioner(z)
+    mom = Moments(z)
     _sync(z)
     t0 = time.perf_counter()
     solves = 0
+    reached = None
     for k in range(steps):
         if encoded:
             encs = [encode(seed * 7919 + i, k, ns) for i in range(nsamp)]
             perm = np.stack([e[0] for e in encs])
             w = np.stack([e[1] for e in encs])
         ctx.gradient(z, perm, w, sg, d_obs, sigma, scale=0.0 if encoded else 1.0, grad=grad)
-        _rms_normalise(grad)
         if prior_lam > 0 or prior_mu > 0:
-            ctx.smooth_prior_grad(z, zref.contiguous(), prior_lam, prior_mu, grad)
-        precond(grad)
-        langevin_step(z, grad, eta, nu, vmin, vmax, seed, k)
+            ctx.smooth_prior_grad(z, zref, prior_lam, prior_mu, grad)
+        refine_step(ctx, z, grad, mom, eta, nu, vmin, vmax, seed, k, eps=eps)
         solves += 2 * len(sg) * nsamp
         if (k + 1) % record_every == 0:
             hist_r.append(_rmse(z.mean(0), truth))
             hist_s.append(solves)
+            if rmse_target is not None and hist_r[-1] <= rmse_target:
+                _sync(z)
+                reached = {"solves": solves, "seconds": time.perf_counter() - t0, "steps": k + 1}
+                break
     _sync(z)
-    return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0, "samples": z}
+    return {"rmse": hist_r, "solves": hist_s, "seconds": time.perf_counter() - t0, "samples": z,
+            "reached": reached}
 
 
-def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_start, stride, K, eta, nu, vmin, vmax,
-                              sigma, denoiser=None, seed=0, renoise_on=True, refine="langevin", state=None,
-                              stop_at=None):
+def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_start, stride, K, eta, vmin, vmax,
+                              sigma, nu=None, denoiser=None, seed=0, renoise_on=True, refine="langevin", state=None,
+                              stop_at=None, eps=0.1):
     """Decoupled encoded-shot diffusion sampler (Sec. 2.3, Algorithm table).
 
-    refine: "langevin" -- K Langevin steps per guided level (Sec. 2.3 (ii));
+    refine: "langevin" -- K preconditioned Langevin steps with matched noise
+                          per guided level (Sec. 2.3 (ii), Sec. 5; nu None:
+                          sqrt(2 eta));
             "adam"     -- K deterministic Adam steps on the same encoded
                           likelihood instead (the deterministic refinement of
                           Sec. 3.2, A15), no injected noise.  The two differ only
@@ -230,7 +225,7 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
     if refine not in ("langevin", "adam"):
         raise ValueError("refine must be 'langevin' or 'adam'")
     run_key = [int(seed), int(nsamp), [int(v) for v in sg_sizes], int(t_start), int(stride), int(K), refine,
-               bool(renoise_on)]
+               bool(renoise_on), float(eta), None if nu is None else float(nu), float(eps)]
     shape = (nsamp,) + tuple(v_init.shape)
     if state is None:
         gen = torch.Generator(device=dev).manual_seed(seed)
@@ -241,8 +236,8 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
             raise ValueError("state was saved by a run with other arguments: %s" % (state["run"],))
         x_t = state["x_t"].to(dev).clone().contiguous()
     grad = torch.empty_like(x_t)
-    precond = RMSPreconditioner(x_t) if refine == "langevin" else AdamState(x_t)
-    step_nu = nu if refine == "langevin" else 0.0
+    nu = math.sqrt(2.0 * eta) if nu is None else nu
+    precond = Moments(x_t, adam=(refine == "adam"))
     if state is None:
         hist_r, hist_s = [_rmse(v_init, truth)], [0]
         solves, it, t_first = 0, 0, t_start
@@ -269,10 +264,8 @@ def encoded_diffusion_sampler(ctx, v_init, d_obs, truth, nsamp, sg_sizes, t_star
                 perm = np.stack([e[0] for e in encs])
                 w = np.stack([e[1] for e in encs])
                 ctx.gradient(z, perm, w, sg_sizes, d_obs, sigma, grad=grad)
-                if refine == "langevin":
-                    _rms_normalise(grad)
-                precond(grad)
-                langevin_step(z, grad, eta, step_nu, vmin, vmax, seed + 1, it)
+                refine_step(ctx, z, grad, precond, eta, nu, vmin, vmax, seed + 1, it, eps=eps,
+                            adam=(refine == "adam"))
                 solves += 2 * nsg * nsamp
                 it += 1
             x0 = normalize(z, vmin, vmax).contiguous()

@@ -155,6 +155,40 @@ def test_langevin_matches_oracle(P, torch):
     assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-6
 
 
+def test_langevin_precond_matches_oracle(P, torch):
+    # three consecutive preconditioned Langevin steps (noise matched to the
+    # preconditioner) and three Adam steps on three samples whose gradients
+    # differ in scale by 1e3, against the oracle; moments carried on both sides
+    w = synth.tiny2d(nz=37, nx=53, nt=20)
+    ctx = make_ctx(P, w, 3)
+    rng = np.random.default_rng(4)
+    shape = (3,) + w.shape
+    z0 = rng.uniform(1600, 3400, shape).astype(np.float32)
+    for use_m, nu in ((False, math.sqrt(2 * 20.0)), (True, 0.0)):
+        zt = torch.tensor(z0).cuda()
+        vt = torch.zeros_like(zt)
+        mt = torch.zeros_like(zt) if use_m else None
+        z, v, m = z0.astype(np.float64), np.zeros(shape), (np.zeros(shape) if use_m else None)
+        for k in range(1, 4):
+            g = (rng.normal(0, 1, shape) * np.array([1.0, 1e3, 1e-3])[:, None, None]).astype(np.float32)
+            g[0, 5, 7] = 0.0
+            ctx.langevin_precond(zt, torch.tensor(g).cuda(), vt, k, 20.0, nu, 1500.0, 3500.0, 31, 100 + k, m=mt,
+                                 alpha=0.99, beta1=0.9, eps=1e-2)
+            z, v, m = O.langevin_precond(z, g, v, m, 20.0, nu, 1500.0, 3500.0, 31, 100 + k, k=k, alpha=0.99,
+                                         beta1=0.9, eps=1e-2)
+            got = zt.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(got - z) / np.abs(z)) < 1e-6, (use_m, k)
+            assert np.max(np.abs(vt.cpu().numpy() - v) / np.maximum(np.abs(v), 1e-30)) < 1e-6
+            if use_m:
+                assert np.max(np.abs(mt.cpu().numpy() - m)) < 1e-6 * np.max(np.abs(m))
+    # invalid arguments are refused on the host
+    zt = torch.tensor(z0).cuda()
+    with pytest.raises(P.FwiError):
+        ctx.langevin_precond(zt, zt.clone(), torch.zeros_like(zt), 3, 1.0, 1.0, 0.0, 1e4, 1, 1, alpha=1.0)
+    with pytest.raises(ValueError, match="v"):
+        ctx.langevin_precond(zt, zt.clone(), torch.zeros(3, 5, device="cuda"), 1, 1.0, 1.0, 0.0, 1e4, 1, 1)
+
+
 def test_renoise_matches_oracle(P, torch):
     beta, abar = O.ddpm_schedule()
     t = 200
@@ -281,6 +315,14 @@ def test_binding_rejects_mis_sized_buffers(P, torch):
         ctx.gradient(v, perm, wt, [w.ns], d_obs, 1.0, grad=torch.empty(2, *w.shape, device="cuda"))
     with pytest.raises(ValueError, match="d_cot"):
         ctx.adjoint(v, perm, wt, [w.ns], torch.zeros(1, 2, w.nt, w.nr, device="cuda"))
+    with pytest.raises(ValueError, match="grad"):
+        P.langevin_step(v, v[:, :-1].contiguous(), 1.0, 1.0, 0.0, 1e4, 1, 1)
+    with pytest.raises(ValueError, match="x0"):
+        P.renoise(v, v[:, :-1].contiguous(), 0.5, 0.6, 1 - 0.5 / 0.6, 1, 1)
+    with pytest.raises(ValueError, match="out"):
+        P.renoise(v, v, 0.5, 0.6, 1 - 0.5 / 0.6, 1, 1, out=torch.empty(3, device="cuda"))
+    with pytest.raises(ValueError, match="grad"):
+        ctx.langevin_precond(v, v[:, :-1].contiguous(), torch.zeros_like(v), 1, 1.0, 1.0, 0.0, 1e4, 1, 1)
     assert ctx.device_status() == 0
 
 

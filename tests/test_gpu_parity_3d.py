@@ -122,3 +122,30 @@ def test_checkpointed_gradient_3d_bit_exact(P):
     assert big.plan_info()["recomputed_steps"] == 0
     assert small.plan_info()["recomputed_steps"] > 0
     assert torch.equal(g1, g2) and torch.equal(m1, m2)
+
+
+def test_chunked_gradient_3d_bit_identical(P):
+    # a workspace too small for all samples' checkpoint plans at once makes
+    # fwi_gradient process the 3D batch in chunks of one sample; every
+    # sample's arithmetic is unchanged, so the results are bit-identical
+    import torch
+    w = medium3d(nt=120)
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 60 + s, 1500, 3000)
+                               for s in range(3)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 10)).cuda()
+    encs = [P.encode(6, s, w.ns) for s in range(3)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    big = P.FWI(w.grid_dict(), w.src, w.rec, 6, 1 << 32)
+    m1, g1 = big.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    assert big.plan_info()["samples_per_chunk"] == 3
+    nzp, nyp, nxp = w.nz + 20, w.ny + 20, w.nx + 20
+    field = (nzp + 8) * (nyp + 8) * ((nxp + 8 + 31) // 32 * 32) * 4
+    # 60 slots of one sample's two wavefields: 30 slots for two samples, fewer
+    # than any plan for 120 steps needs
+    small = P.FWI(w.grid_dict(), w.src, w.rec, 6, 60 * 2 * field)
+    m2, g2 = small.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+    torch.cuda.synchronize()
+    assert small.plan_info()["samples_per_chunk"] == 1
+    assert small.plan_info()["recomputed_steps"] > 0
+    assert torch.equal(g1, g2) and torch.equal(m1, m2)

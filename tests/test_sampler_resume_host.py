@@ -24,15 +24,24 @@ class FakeCtx:
         grad.copy_((z - d_obs) * (1.0 + 0.05 * wsum) / sigma ** 2)
         return None, grad
 
+    def langevin_precond(self, z, grad, v, k, eta, nu, vmin, vmax, seed, counter, m=None, alpha=0.9, beta1=0.9,
+                         eps=1e-2, stream=None):
+        # the moment bookkeeping of the library call, on the CPU
+        v.mul_(alpha).addcmul_(grad, grad, value=1 - alpha)
+        vh = v / (1 - alpha ** k)
+        d = grad
+        if m is not None:
+            m.mul_(beta1).add_(grad, alpha=1 - beta1)
+            d = m / (1 - beta1 ** k)
+        r = vh.reshape(vh.shape[0], -1).mean(1).sqrt().view(-1, 1, 1)
+        G = 1.0 / (vh.sqrt() + eps * r)
+        z.sub_(eta * G * d).add_(nu * G.sqrt() * _noise(seed, counter, z)).clamp_(vmin, vmax)
+        return z
+
 
 def _noise(seed, counter, like):
     g = torch.Generator().manual_seed((seed * 1000003 + counter) % (2 ** 63))
     return torch.randn(like.shape, generator=g, dtype=like.dtype)
-
-
-def fake_langevin(z, grad, eta, nu, vmin, vmax, seed, counter, stream=None):
-    z.sub_(eta * grad).add_(nu * _noise(seed, counter, z)).clamp_(vmin, vmax)
-    return z
 
 
 def fake_renoise(x_t, x0, abar_t, abar_prev, beta_t, seed, counter, out=None, stream=None):
@@ -44,7 +53,6 @@ def fake_renoise(x_t, x0, abar_t, abar_prev, beta_t, seed, counter, out=None, st
 
 @pytest.fixture
 def fakes(monkeypatch):
-    monkeypatch.setattr(S, "langevin_step", fake_langevin)
     monkeypatch.setattr(S, "renoise", fake_renoise)
 
 
