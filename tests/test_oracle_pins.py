@@ -188,6 +188,12 @@ def test_sponge_absorbs_reflections():
     # enough that nothing returns within the window: the difference is what the
     # boundary sends back.  The damping sponge must cut it several-fold against a
     # hard (undamped, zero-halo) boundary and keep cutting it as it widens.
+    # R = 1e-3 bounds only what crosses the whole sponge and returns (the
+    # round-trip attenuation exp(-2 int gamma/v) = R at normal incidence); the
+    # damping profile's own gradient reflects more.  Measured relative L2:
+    # hard wall 1.10, 20 cells 0.209, 40 cells 0.035, 60 cells 0.011 -- the
+    # bounds below hold these with a margin, so a profile off by a factor
+    # (gamma_max, the (d/nb)^2 shape) fails them.
     v, h, dt, nt, f0 = 2000.0, 10.0, 1e-3, 800, 10.0
     n = 81
     N = 3 * n
@@ -203,8 +209,9 @@ def test_sponge_absorbs_reflections():
 
     hard, r20, r40 = refl(20, 1e-9), refl(20, v), refl(40, v)
     assert hard > 0.8
-    assert r20 < 0.25 * hard
-    assert r40 < 0.5 * r20
+    assert 0.15 < r20 < 0.23
+    assert 0.02 < r40 < 0.045
+    assert r40 < 0.25 * r20
 
 
 def test_encoded_forward_is_weighted_sum_of_shots():
