@@ -34,6 +34,14 @@
  *     frees caller memory and keeps no caller pointer after a call returns.
  *   - stream is a cudaStream_t (NULL = legacy default stream).  Device work is
  *     enqueued asynchronously on it; calls return once the work is enqueued.
+ *     Calls on one context use one stream.  The calls of a context do not
+ *     wait for the device, with three exceptions: the first fwi_forward or
+ *     fwi_gradient for a given number of wavefields times the step-kernel
+ *     variants (see fwi_set_kernel_variants); the per-call point lists and
+ *     step descriptors go through 4 pinned staging buffers each, used in
+ *     turn, so an upload waits for the copy issued 4 uploads earlier (the
+ *     host can run 4 gradient chunks ahead); and the profiling and status
+ *     queries below synchronise as documented.
  *   - Return value: FWI_OK or a negative fwi_status.  Argument, geometry,
  *     stability and allocation errors are detected on the host and returned
  *     before anything is enqueued.  Errors found on the device (non-finite
@@ -304,13 +312,17 @@ int fwi_checkpoint_schedule(int nt, int64_t slots, int32_t* desc_out, int cap, i
  * minimises (chunks) x (2 nt + recomputed steps) x (time of one step launch). */
 int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
 
-/* Step-kernel variants (tile rows per thread, TMA ring depth).  By default the
- * first fwi_forward / fwi_gradient call for a given nsamp*nsg times every
- * compiled variant on that shape (synchronising the stream while it does)
- * and keeps the fastest; all variants give bit-identical results.
- * fwi_set_kernel_variants forces a variant index (-1 restores autotuning);
- * fwi_kernel_variants reports the chosen indices and names and, in ms[0..7],
- * the per-launch time of each variant measured by the tuner (-1: not run). */
+/* Step-kernel variants: in 2D the TMA ring depth, in 3D the CTA order
+ * (0: all tiles of one wavefield back to back, 1: the tile of every wavefield
+ * of the launch side by side, so that a sample's supergathers share its cc
+ * reads through L2).  By default the first fwi_forward / fwi_gradient call
+ * for a given nsamp*nsg times every variant on that shape (synchronising the
+ * stream while it does) and keeps the fastest; all variants give
+ * bit-identical results.  fwi_set_kernel_variants forces a variant index (-1
+ * restores autotuning; FWI_ERR_ARG beyond the variant count);
+ * fwi_kernel_variants reports the chosen indices and names and, in
+ * ms[0..7], the per-step time of each variant measured by the tuner (-1: not
+ * run). */
 int fwi_set_kernel_variants(fwi_ctx* ctx, int fwd, int adj);
 int fwi_kernel_variants(fwi_ctx* ctx, int* fwd, int* adj, const char** fwd_name, const char** adj_name,
                         float* fwd_ms, float* adj_ms, int* nvariants);

@@ -110,6 +110,11 @@ bool make_plan(int nt, long long avail, Plan* out) {
 }
 
 constexpr int kTuneSteps = 6;  // steps per autotuner timing launch
+// Pinned staging buffers per kind (point lists, step descriptors), used in
+// turn: an upload waits only for the copy issued kStaging uploads earlier,
+// so the host can run that many gradient chunks ahead of the device before
+// a call blocks.
+constexpr int kStaging = 4;
 
 // NVTX ranges (profiler annotations; no-ops when no tool is attached): one
 // for the call, and inside it one for each phase in turn.  The destructor
@@ -171,9 +176,10 @@ struct fwi_ctx {
   int4* rec_inj = nullptr;   // adjoint injection entries (z in .w)
   // per-call lists
   unsigned char* dlist = nullptr;
-  unsigned char* hlist = nullptr;  // pinned staging
+  unsigned char* hlist[kStaging] = {};  // pinned staging, used in turn
   size_t list_bytes = 0;
-  cudaEvent_t ev_list = nullptr;
+  cudaEvent_t ev_list[kStaging] = {};
+  int list_turn = 0;
   // profiling
   bool prof = false;
   cudaEvent_t ev[5] = {};
@@ -194,9 +200,10 @@ struct fwi_ctx {
   // staging, host copy), the autotuner's steps, and the per-item progress
   // flags of the multi-step 2D launches
   StepDesc* desc = nullptr;
-  StepDesc* hdesc = nullptr;
+  StepDesc* hdesc[kStaging] = {};
   size_t desc_cap = 0;
-  cudaEvent_t ev_desc = nullptr;
+  cudaEvent_t ev_desc[kStaging] = {};
+  int desc_turn = 0;
   std::vector<StepDesc> descs;
   StepDesc* tdesc = nullptr;
   int* done = nullptr;  // [max_B * ntiles]
@@ -416,9 +423,12 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
   cl->src_amp = take((size_t)B * std::max(C->Emax, 1) * 4);
   cl->total = p;
   if (p > C->list_bytes) return FWI_ERR_ARG;
-  // the previous call's upload must have left the staging buffer
-  CK(cudaEventSynchronize(C->ev_list));
-  unsigned char* h = C->hlist;
+  // this turn's staging buffer: its previous upload (kStaging uploads ago)
+  // must have left it
+  const int turn = C->list_turn;
+  C->list_turn = (turn + 1) % kStaging;
+  CK(cudaEventSynchronize(C->ev_list[turn]));
+  unsigned char* h = C->hlist[turn];
   const float inv_vol = (float)(1.0 / C->cell_volume);
   build_csr(C, lists, reinterpret_cast<int*>(h + cl->inj_off), [&](int pos, int local, const Entry& e) {
     int4 v;
@@ -460,8 +470,8 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
       amp[(size_t)b * C->Emax + e] = en.amp * inv_vol;
     }
   }
-  CK(cudaMemcpyAsync(C->dlist, C->hlist, cl->total, cudaMemcpyHostToDevice, st));
-  CK(cudaEventRecord(C->ev_list, st));
+  CK(cudaMemcpyAsync(C->dlist, h, cl->total, cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(C->ev_list[turn], st));
   *Emax_out = Emax;
   return FWI_OK;
 }
@@ -510,6 +520,8 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
       P.s_out = d.out;
       P.s_snap = d.snap;
       P.t = d.t;
+      P.order3 = C->var[adj ? 1 : 0] & 1;
+      P.zpair3 = C->var[adj ? 1 : 0] >> 1;
       CK(launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st));
     }
     *launches += n;
@@ -528,10 +540,12 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
 int upload_descs(fwi_ctx* C, cudaStream_t st) {
   const size_t n = C->descs.size();
   if (n > C->desc_cap) return FWI_ERR_ARG;
-  CK(cudaEventSynchronize(C->ev_desc));  // the previous copy out of the staging buffer is done
-  memcpy(C->hdesc, C->descs.data(), n * sizeof(StepDesc));
-  CK(cudaMemcpyAsync(C->desc, C->hdesc, n * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
-  CK(cudaEventRecord(C->ev_desc, st));
+  const int turn = C->desc_turn;  // staging buffer of this upload (see kStaging)
+  C->desc_turn = (turn + 1) % kStaging;
+  CK(cudaEventSynchronize(C->ev_desc[turn]));
+  memcpy(C->hdesc[turn], C->descs.data(), n * sizeof(StepDesc));
+  CK(cudaMemcpyAsync(C->desc, C->hdesc[turn], n * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(C->ev_desc[turn], st));
   return FWI_OK;
 }
 
@@ -546,34 +560,65 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
   return d;
 }
 
-// Autotuner: time every compiled variant of the forward and adjoint step
-// kernels on this call's shape (B wavefields over the real tiles, zero inputs
-// read from the zero slot, output to a ring slot, no injection or sampling)
-// and keep the fastest.  Runs once per wavefield count; synchronises the
-// stream while it times.
-int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
-             long long nslots, cudaStream_t st) {
-  const int B = nsamp * nsg;
+// Step-kernel variants: 2D ring depths (stencil.cu); 3D CTA orders.
+// 3D variant v: bit 0 the CTA order, bit 1 two z levels per march step.
+int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 4 : num_variants2d(adj); }
+const char* variant_name(const fwi_ctx* C, bool adj, int v) {
+  if (C->L.ndim == 2) return variant2d_name(adj, v);
+  static const char* names[2][4] = {
+      {"fwd3d tile-major, 1 level", "fwd3d wavefield-fastest, 1 level", "fwd3d tile-major, 2 levels",
+       "fwd3d wavefield-fastest, 2 levels"},
+      {"adj3d tile-major, 1 level", "adj3d wavefield-fastest, 1 level", "adj3d tile-major, 2 levels",
+       "adj3d wavefield-fastest, 2 levels"}};
+  return v < 0 || v > 3 ? "-" : names[adj ? 1 : 0][v];
+}
+
+// kTuneSteps steps of variant v: one multi-step launch in 2D, one launch per
+// step in 3D (slots from td).
+cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDesc* td, int nsamp, int B,
+                        const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg,
+                        cudaStream_t st) {
   if (C->L.ndim == 3) {
-    C->var[0] = C->var[1] = 0;
-    return FWI_OK;
+    P.order3 = v & 1;
+    P.zpair3 = v >> 1;
+    for (int i = 0; i < kTuneSteps; i++) {
+      P.s_cur = td[i].cur;
+      P.s_prev = td[i].prev;
+      P.s_out = td[i].out;
+      P.s_snap = td[i].snap;
+      cudaError_t e = launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
+  cudaError_t e = cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st);
+  if (e != cudaSuccess) return e;
+  return launch_step2d(adj, v, th, tp, tc, C->L, C->K, P, nsamp, st);
+}
+
+// Autotuner: time every variant of the forward and adjoint step kernels on
+// this call's shape (B wavefields over the real tiles, whatever the three ring
+// slots hold, no injection or sampling) and keep the fastest.  Runs once per
+// wavefield count; synchronises the stream while it times.  All variants give
+// bit-identical results.  The 3D adjoint variant writes the imaging
+// accumulator, which every gradient chunk clears after tuning.
+int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
+             const CUtensorMap& tg, long long nslots, cudaStream_t st) {
+  const int B = nsamp * nsg;
   if (C->tuned_B == B && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
   // timing steps with the traffic of real ones: the three ring slots rotate
   // (whatever they hold), the snapshot comes from a fourth slot when there is one
-  {
-    StepDesc td[kTuneSteps];
-    for (int i = 0; i < kTuneSteps; i++)
-      td[i] = make_desc(Plan::RING + i % 3, Plan::RING + (i + 2) % 3, Plan::RING + (i + 1) % 3,
-                        nslots > Plan::QR ? Plan::QR : Plan::ZERO, 0);
-    CK(cudaStreamSynchronize(st));
-    CK(cudaMemcpy(C->tdesc, td, sizeof(td), cudaMemcpyHostToDevice));
-  }
+  StepDesc td[kTuneSteps];
+  for (int i = 0; i < kTuneSteps; i++)
+    td[i] = make_desc(Plan::RING + i % 3, Plan::RING + (i + 2) % 3, Plan::RING + (i + 1) % 3,
+                      nslots > Plan::QR ? Plan::QR : Plan::ZERO, 0);
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(C->tdesc, td, sizeof(td), cudaMemcpyHostToDevice));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   for (int adj = 0; adj < 2; adj++) {
-    const int nv = num_variants2d(adj != 0);
+    const int nv = num_variants(C, adj != 0);
     if (C->forced[adj] >= 0 && C->forced[adj] < nv) {
       C->var[adj] = C->forced[adj];
       continue;
@@ -586,21 +631,16 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtens
     P.steps = C->tdesc;
     P.nsteps = kTuneSteps;
     P.done = C->done;
-    const size_t done_bytes = (size_t)nsamp * C->ntiles * 4;
     int best = -1;
     float best_ms = 1e30f;
     for (int v = 0; v < nv && v < 8; v++) {
       C->tune_ms[adj][v] = -1.f;
-      CK(cudaMemsetAsync(C->done, 0, done_bytes, st));
-      if (launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st) != cudaSuccess) {
+      if (launch_tune(C, adj != 0, v, P, td, nsamp, B, th, tp, tc, tg, st) != cudaSuccess) {
         cudaGetLastError();  // variant does not fit this device: skip it
         continue;
       }
       CK(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; r++) {
-        CK(cudaMemsetAsync(C->done, 0, done_bytes, st));
-        CK(launch_step2d(adj != 0, v, th, tp, tc, C->L, C->K, P, nsamp, st));
-      }
+      for (int r = 0; r < 3; r++) CK(launch_tune(C, adj != 0, v, P, td, nsamp, B, th, tp, tc, tg, st));
       CK(cudaEventRecord(e1, st));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -781,19 +821,34 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
   C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 16 + 8 + 4) +
                   (size_t)(B + 1) * 4 + (size_t)B * C->ns * 8 + (size_t)B * 4 + 64 * 256;
   if (!alloc((void**)&C->dlist, C->list_bytes) ||
-      cudaHostAlloc((void**)&C->hlist, C->list_bytes, cudaHostAllocDefault) != cudaSuccess) {
+      [&] {
+        for (int i = 0; i < kStaging; i++)
+          if (cudaHostAlloc((void**)&C->hlist[i], C->list_bytes, cudaHostAllocDefault) != cudaSuccess) return true;
+        return false;
+      }()) {
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
-  if (cudaEventCreateWithFlags(&C->ev_list, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&C->ev_desc, cudaEventDisableTiming) != cudaSuccess) {
+  if ([&] {
+        for (int i = 0; i < kStaging; i++)
+          if (cudaEventCreateWithFlags(&C->ev_list[i], cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&C->ev_desc[i], cudaEventDisableTiming) != cudaSuccess)
+            return true;
+        return false;
+      }()) {
     fwi_destroy(C);
     return FWI_ERR_CUDA;
   }
   // step descriptors: forward, recomputed and adjoint steps of one call
   C->desc_cap = 3 * (size_t)g->nt + 16;
   if (!alloc((void**)&C->desc, C->desc_cap * sizeof(StepDesc)) ||
-      cudaHostAlloc((void**)&C->hdesc, C->desc_cap * sizeof(StepDesc), cudaHostAllocDefault) != cudaSuccess ||
+      [&] {
+        for (int i = 0; i < kStaging; i++)
+          if (cudaHostAlloc((void**)&C->hdesc[i], C->desc_cap * sizeof(StepDesc), cudaHostAllocDefault) !=
+              cudaSuccess)
+            return true;
+        return false;
+      }() ||
       !alloc((void**)&C->tdesc, kTuneSteps * sizeof(StepDesc)) ||
       !alloc((void**)&C->done, (size_t)B * C->ntiles * 4)) {
     fwi_destroy(C);
@@ -850,10 +905,12 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->desc);
   cudaFree(C->tdesc);
   cudaFree(C->done);
-  if (C->hlist) cudaFreeHost(C->hlist);
-  if (C->hdesc) cudaFreeHost(C->hdesc);
-  if (C->ev_list) cudaEventDestroy(C->ev_list);
-  if (C->ev_desc) cudaEventDestroy(C->ev_desc);
+  for (int i = 0; i < kStaging; i++) {
+    if (C->hlist[i]) cudaFreeHost(C->hlist[i]);
+    if (C->hdesc[i]) cudaFreeHost(C->hdesc[i]);
+    if (C->ev_list[i]) cudaEventDestroy(C->ev_list[i]);
+    if (C->ev_desc[i]) cudaEventDestroy(C->ev_desc[i]);
+  }
   for (int i = 0; i < 5; i++)
     if (C->ev[i]) cudaEventDestroy(C->ev[i]);
   delete C;
@@ -929,7 +986,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   if (nslots < 4) return FWI_ERR_OOM;
   CUtensorMap th, tp, tc, tg;
   if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, nslots, st)) != FWI_OK) return rc;
+  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, tg, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
@@ -968,7 +1025,7 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   C->slots_avail = nslots;
   CUtensorMap th, tp, tc, tg;
   if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, nslots, st)) != FWI_OK) return rc;
+  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, tg, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
@@ -1246,7 +1303,7 @@ int fwi_plan_info(fwi_ctx* C, int* K, int* nseg, int64_t* rec, int* used, int* a
 
 int fwi_set_kernel_variants(fwi_ctx* C, int fwd, int adj) {
   if (!C) return FWI_ERR_ARG;
-  if (C->L.ndim == 2 && (fwd >= num_variants2d(false) || adj >= num_variants2d(true))) return FWI_ERR_ARG;
+  if (fwd >= num_variants(C, false) || adj >= num_variants(C, true)) return FWI_ERR_ARG;
   C->forced[0] = fwd < 0 ? -1 : fwd;
   C->forced[1] = adj < 0 ? -1 : adj;
   C->tuned_B = -1;
@@ -1256,12 +1313,11 @@ int fwi_set_kernel_variants(fwi_ctx* C, int fwd, int adj) {
 int fwi_kernel_variants(fwi_ctx* C, int* fwd, int* adj, const char** fwd_name, const char** adj_name,
                         float* fwd_ms, float* adj_ms, int* nvariants) {
   if (!C) return FWI_ERR_ARG;
-  const bool d2 = C->L.ndim == 2;
   if (fwd) *fwd = C->var[0];
   if (adj) *adj = C->var[1];
-  if (fwd_name) *fwd_name = d2 ? variant2d_name(false, C->var[0]) : "fwd3d";
-  if (adj_name) *adj_name = d2 ? variant2d_name(true, C->var[1]) : "adj3d";
-  const int n = d2 ? std::max(num_variants2d(false), num_variants2d(true)) : 1;
+  if (fwd_name) *fwd_name = variant_name(C, false, C->var[0]);
+  if (adj_name) *adj_name = variant_name(C, true, C->var[1]);
+  const int n = std::max(num_variants(C, false), num_variants(C, true));
   if (nvariants) *nvariants = n;
   for (int v = 0; v < n && v < 8; v++) {
     if (fwd_ms) fwd_ms[v] = C->tune_ms[0][v];

@@ -80,6 +80,8 @@ struct StepParams {
   // (item = tile of one sample, flag = steps completed; zero at launch)
   const StepDesc* steps; int nsteps;
   int* done;
+  int order3;               // 3D CTA order: 0 tile-major, 1 wavefield-fastest
+  int zpair3;               // 3D march: 0 one level at a time, 1 two levels together
 };
 
 // Host-side launchers (stencil.cu)

@@ -59,7 +59,7 @@ __device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 
 
 // Laplacian of the thread's 4 points: x and y neighbours from the halo plane H
 // (row ly+4, columns lx..lx+11, row stride HX3), z neighbours from the circular register queue
-// Q (Q[(C+k) % 9] holds level z+k, k = -4..4, C the index of the centre).
+// Q of NQ levels (Q[(C+k) % NQ] holds level z+k, k = -4..4, C the index of the centre).
 // Adjacent columns are computed as pairs with the packed FP32 instructions;
 // each point sees the operations of the scalar form in the same order
 // (x - y as fma(y, -1, x), exact).  ISO (hx == hy == hz): the axes share
@@ -67,12 +67,12 @@ __device__ __forceinline__ float2 half2of(const float4& v, int j) { return j == 
 //   [(x_{+k} + x_{-k}) + (y_{+k} + y_{-k}) - 4p] + [(z_{+k} + z_{-k}) - 2p],
 // which is still exactly zero on a constant field, so the chain of
 // coefficient FMAs is 4 long instead of 12.
-template <int C, bool ISO>
-__device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[9], int ly, int lx,
+template <int C, bool ISO, int NQ>
+__device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (&Q)[NQ], int ly, int lx,
                                      const Coef& K, float (&lap)[4]) {
   const float* row = H + (ly + HALO) * HX3;
   const float4 xl = ld4s(row + lx), xr = ld4s(row + lx + 8);
-  const float4 ce = Q[C % 9];
+  const float4 ce = Q[C % NQ];
   const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
   float4 yn[8];
 #pragma unroll
@@ -91,7 +91,7 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
                      : __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k]));
     };
     auto ys = [&](int k) { return __fadd2_rn(half2of(yn[k + 3], j), half2of(yn[k - 1], j)); };
-    auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % 9], j), half2of(Q[(C + 9 - k) % 9], j)); };
+    auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % NQ], j), half2of(Q[(C + NQ - k) % NQ], j)); };
     if (ISO) {
       const float2 m4 = f2(-4.f, -4.f);
       auto br = [&](int k) {
@@ -122,7 +122,7 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   }
 }
 
-template <bool ADJ, bool ISO>
+template <bool ADJ, bool ISO, int NQ>
 struct March3D {
   using S = Smem3D<ADJ>;
   static constexpr int NST = S::NST;
@@ -142,12 +142,13 @@ struct March3D {
   float gyv, gxv[4];
   const float* gz;       // shared gamma*dt per z level
   int pq, pst;           // producer: next sequence, its slot
-  int cslot, hslot;      // consumer: slots of sequences q and q - 4 (running, no division)
-  uint32_t cphase;       // consumer: (q / NST) & 1
+  int cslot;             // consumer, landing side: slot of the next sequence to land (running)
+  uint32_t cphase;       // consumer: its phase, (q / NST) & 1
+  int lslot, hslot;      // consumer, level side: slots of sequences q and q - 4 (running, no division)
   uint32_t pround;
   int ie_cur, ie_end, se_cur, se_end;  // point-list cursors (entries sorted by z)
   int inj_z, smp_z;                    // z of the entries under the cursors (INT_MAX: none left)
-  float4 Q[9], QS[9];
+  float4 Q[NQ], QS[NQ];
 
   __device__ __forceinline__ void issue() {
     const int zh = pq - HALO, zp = pq - 2 * HALO;
@@ -167,20 +168,32 @@ struct March3D {
   }
 
 
-  // Sequence q with the queue centre at compile-time index C = (q - 4) % 9.
+  // Landing of the next sequence q: waits for its slot and moves the centre
+  // of its halo plane (level q - 4) into queue index CI = (q - 4 + 4) % NQ.
+  template <int CI>
+  __device__ __forceinline__ bool land() {
+    if (!mbar_wait_abortable(&full[cslot], cphase, P.status, abort_flag)) return false;
+    const float* stage = sm + cslot * S::STAGE;
+    Q[CI] = ld4s(stage + (ly + HALO) * HX3 + lx + HALO);
+    if (ADJ) QS[CI] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX3 + lx + HALO);
+    if (++cslot == NST) {
+      cslot = 0;
+      cphase ^= 1u;
+    }
+    return true;
+  }
+
+  // Level z = q - 8 from landed sequences q (plain planes) and q - 4 (halo
+  // plane), queue centre at compile-time index C = (q - 4) % NQ; then the
+  // slot of sequence q - 4 is released.
   template <int C>
-  __device__ __forceinline__ bool step(int q) {
-    const int slot = cslot;
-    if (!mbar_wait_abortable(&full[slot], cphase, P.status, abort_flag)) return false;
-    float* stage = sm + slot * S::STAGE;
-    // the centre of halo plane q-4 enters the queue at index (C + 4) % 9
-    Q[(C + 4) % 9] = ld4s(stage + (ly + HALO) * HX3 + lx + HALO);
-    if (ADJ) QS[(C + 4) % 9] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX3 + lx + HALO);
+  __device__ __forceinline__ void level(int q) {
+    float* stage = sm + lslot * S::STAGE;
     const int z = q - 2 * HALO;
     if (z >= 0) {
       const float* hpl = sm + hslot * S::STAGE;  // halo plane of level z (sequence q - 4)
       float lap[4];
-      lap3<C, ISO>(hpl, Q, ly, lx, K, lap);
+      lap3<C, ISO, NQ>(hpl, Q, ly, lx, K, lap);
       const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX3 + lx);
       const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
       const float gzy = gz[z] + gyv;
@@ -188,7 +201,7 @@ struct March3D {
 #pragma unroll
       for (int j = 0; j < 4; j += 2) {  // cc * lap + (p + b (p - pm)), in pairs
         const float2 bb = f2(sponge_b(gzy + gxv[j]), sponge_b(gzy + gxv[j + 1]));
-        const float2 p = half2of(Q[C % 9], j);
+        const float2 p = half2of(Q[C % NQ], j);
         const float2 d = __ffma2_rn(half2of(pm, j), f2(-1.f, -1.f), p);
         const float2 n2 = __ffma2_rn(half2of(cv, j), f2(lap[j], lap[j + 1]), __ffma2_rn(bb, d, p));
         nv[j] = n2.x;
@@ -230,7 +243,7 @@ struct March3D {
       }
       if (ADJ) {
         float lps[4];
-        lap3<C, ISO>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
+        lap3<C, ISO, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
         const float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (colv) {
           float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
@@ -260,16 +273,12 @@ struct March3D {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[hslot]);
     }
-    if (++cslot == NST) {
-      cslot = 0;
-      cphase ^= 1u;
-    }
+    if (++lslot == NST) lslot = 0;
     if (++hslot == NST) hslot = 0;
-    return true;
   }
 };
 
-template <bool ADJ, bool ISO>
+template <bool ADJ, bool ISO, int NQ>
 __global__ void __launch_bounds__(NTHREADS3, 1)
 step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_cc, const __grid_constant__ CUtensorMap tm_g, const Layout L,
@@ -283,14 +292,23 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST);
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  March3D<ADJ, ISO> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
+  March3D<ADJ, ISO, NQ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
   M.lane = tid & 31;
   M.ly = 2 * warp + (tid >> 4 & 1);
-  M.x0 = blockIdx.x * TX3;
-  M.y0 = blockIdx.y * TY3;
-  M.b = blockIdx.z;
+  // CTA -> (wavefield, tile): tile-major order runs all tiles of a wavefield
+  // back to back; wavefield-fastest order runs the tile of every wavefield
+  // of the launch side by side, so the supergathers of a sample read the
+  // same cc plane within microseconds of each other (one DRAM read, the
+  // others L2 hits)
+  {
+    const int nb = gridDim.x / P.ntiles;
+    const int idx = blockIdx.x;
+    M.b = P.order3 ? idx % nb : idx / P.ntiles;
+    M.tile = P.order3 ? idx / nb : idx % P.ntiles;
+  }
+  M.x0 = (M.tile % P.ntx) * TX3;
+  M.y0 = (M.tile / P.ntx) * TY3;
   M.s = M.b / P.nsg;
-  M.tile = blockIdx.y * P.ntx + blockIdx.x;
   M.lx = 4 * (M.lane & 15);
   M.gx = M.x0 + M.lx;
   M.gy = M.y0 + M.ly;
@@ -301,6 +319,7 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.pst = 0;
   M.pround = 0;
   M.cslot = 0;
+  M.lslot = 0;
   M.hslot = Smem3D<ADJ>::NST - HALO;  // (0 - 4) mod NST: first used at q = 4
   M.cphase = 0;
 
@@ -352,32 +371,50 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.inj_z = M.ie_cur < M.ie_end ? P.inj[M.ie_cur].w : 0x7fffffff;
   M.smp_z = M.se_cur < M.se_end ? P.smp4[M.se_cur].z : 0x7fffffff;
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
+  for (int i = 0; i < NQ; i++) {
     M.Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     M.QS[i] = M.Q[i];
   }
-  // sequence q has queue centre index (q - 4) mod 9 = (q + 5) mod 9
+  // Sequence q lands at queue index q % NQ (the centre of level q - 4) and
+  // level q - 8 has its centre at (q - 4) % NQ.  NQ = 9: one sequence, one
+  // level at a time.  NQ = 10: two sequences land, then their two levels are
+  // computed together (two independent chains per thread), the queue holding
+  // levels z - 4 .. z + 5.
+#define FWI_ONE(k)                                  \
+  if (!M.template land<(k) % NQ>()) return;         \
+  M.template level<((k) + NQ - 4) % NQ>(q + (k));
+#define FWI_TWO(k)                                  \
+  if (!M.template land<(k)>()) return;              \
+  if (!M.template land<(k) + 1>()) return;          \
+  M.template level<((k) + 6) % 10>(q + (k));        \
+  M.template level<((k) + 7) % 10>(q + (k) + 1);
   int q = 0;
-  for (; q + 9 <= M.last_q + 1; q += 9) {
-    if (!M.template step<5>(q)) return;
-    if (!M.template step<6>(q + 1)) return;
-    if (!M.template step<7>(q + 2)) return;
-    if (!M.template step<8>(q + 3)) return;
-    if (!M.template step<0>(q + 4)) return;
-    if (!M.template step<1>(q + 5)) return;
-    if (!M.template step<2>(q + 6)) return;
-    if (!M.template step<3>(q + 7)) return;
-    if (!M.template step<4>(q + 8)) return;
+  if constexpr (NQ == 9) {
+    for (; q + 9 <= M.last_q + 1; q += 9) {
+      FWI_ONE(0) FWI_ONE(1) FWI_ONE(2) FWI_ONE(3) FWI_ONE(4) FWI_ONE(5) FWI_ONE(6) FWI_ONE(7) FWI_ONE(8)
+    }
+    const int rem = M.last_q + 1 - q;
+    if (rem > 0) { FWI_ONE(0) }
+    if (rem > 1) { FWI_ONE(1) }
+    if (rem > 2) { FWI_ONE(2) }
+    if (rem > 3) { FWI_ONE(3) }
+    if (rem > 4) { FWI_ONE(4) }
+    if (rem > 5) { FWI_ONE(5) }
+    if (rem > 6) { FWI_ONE(6) }
+    if (rem > 7) { FWI_ONE(7) }
+  } else {
+    for (; q + 10 <= M.last_q + 1; q += 10) {
+      FWI_TWO(0) FWI_TWO(2) FWI_TWO(4) FWI_TWO(6) FWI_TWO(8)
+    }
+    const int rem = M.last_q + 1 - q;
+    if (rem >= 2) { FWI_TWO(0) } else if (rem == 1) { FWI_ONE(0) }
+    if (rem >= 4) { FWI_TWO(2) } else if (rem == 3) { FWI_ONE(2) }
+    if (rem >= 6) { FWI_TWO(4) } else if (rem == 5) { FWI_ONE(4) }
+    if (rem >= 8) { FWI_TWO(6) } else if (rem == 7) { FWI_ONE(6) }
+    if (rem == 9) { FWI_ONE(8) }
   }
-  const int rem = M.last_q + 1 - q;
-  if (rem > 0 && !M.template step<5>(q)) return;
-  if (rem > 1 && !M.template step<6>(q + 1)) return;
-  if (rem > 2 && !M.template step<7>(q + 2)) return;
-  if (rem > 3 && !M.template step<8>(q + 3)) return;
-  if (rem > 4 && !M.template step<0>(q + 4)) return;
-  if (rem > 5 && !M.template step<1>(q + 5)) return;
-  if (rem > 6 && !M.template step<2>(q + 6)) return;
-  if (rem > 7 && !M.template step<3>(q + 7)) return;
+#undef FWI_ONE
+#undef FWI_TWO
 }
 
 template <bool ADJ, bool ISO>
@@ -385,17 +422,17 @@ static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_pla
                            const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, dim3 grid,
                            cudaStream_t st) {
   const size_t bytes = Smem3D<ADJ>::bytes(L.nzp);
-  cudaError_t e = cudaFuncSetAttribute(step3d_kernel<ADJ, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  auto kern = P.zpair3 ? step3d_kernel<ADJ, ISO, 10> : step3d_kernel<ADJ, ISO, 9>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  step3d_kernel<ADJ, ISO><<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
+  kern<<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
                           const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, int B,
                           cudaStream_t st) {
-  const int nty = (L.nyp + TY3 - 1) / TY3;
-  dim3 grid(P.ntx, nty, B);
+  dim3 grid((unsigned)(P.ntiles * B));
   // The one-bracket form serves the forward only: on the layered 3D batch
   // it made the forward step 4 % faster and the adjoint step (two
   // Laplacians) 2 % slower.

@@ -149,3 +149,29 @@ def test_chunked_gradient_3d_bit_identical(P):
     assert small.plan_info()["samples_per_chunk"] == 1
     assert small.plan_info()["recomputed_steps"] > 0
     assert torch.equal(g1, g2) and torch.equal(m1, m2)
+
+
+def test_3d_step_variants_bit_identical(P):
+    # the autotuner's 3D variants (CTA order; one or two z levels per march
+    # step) change only which CTA runs which tile when and how a thread's
+    # instructions interleave, not any point's arithmetic, so forced choices
+    # give bit-identical gradients
+    import torch
+    w = medium3d(nt=60)
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 70 + s, 1500, 3000)
+                               for s in range(2)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 11)).cuda()
+    encs = [P.encode(8, s, w.ns) for s in range(2)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    out = []
+    for var in ((0, 0), (1, 1), (2, 3), (3, 2)):
+        ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
+        ctx.set_variants(*var)
+        out.append(ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0))
+        got = ctx.variants()
+        assert (got["forward"], got["adjoint"]) == var
+        ctx.close()
+    torch.cuda.synchronize()
+    for m, g in out[1:]:
+        assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0])
