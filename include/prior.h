@@ -77,6 +77,39 @@ int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D
 int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, int P, int Cout, int Cin, int splits,
                                int* status, void* stream);
 
+// The memory-bound layers around the convolutions (csrc/prior_ops.cu); all
+// activations are BF16 NHWC with C a multiple of 8, pointers 16-byte aligned.
+//
+// First layer of the network: the input image is the noisy model scaled,
+// y = scale * x (x_t / sqrt(abar_t) for scale = 1/sqrt(abar_t), Sec. 2.2),
+// edge-replicated from [H][W] to the tiled shape [Hp][Wp], as channel 0, and
+// the noise level sigma[n] as channel 1, both rounded to BF16; then the same
+// 3x3 convolution as prior_conv3x3_bf16 (zero padding 1 around [Hp][Wp]),
+//   Y[n][h][w][o] = relu?(bias[o] + sum_{dy,dx} sum_{c<2} Wt[o][dy*3+dx][c] * in_c(h+dy-1, w+dx-1)),
+// with FP32 accumulation on the CUDA cores (18 products per output).
+//   x: [nimg][H][W] FP32; sigma: [nimg] FP32; Wt: [Cout][9][2] BF16; bias: [Cout] FP32 or null;
+//   Y: [nimg][Hp][Wp][Cout] BF16; 8 <= Cout <= 256, Cout % 8 == 0.
+int prior_first_conv_bf16(const float* x, int nimg, int H, int W, int Hp, int Wp, float scale, const float* sigma,
+                          const void* Wt, const float* bias, int Cout, int relu, void* Y, void* stream);
+
+// 2 x 2 average pooling: Y[n][h][w][c] = BF16(FP32 sum of X[n][2h..2h+1][2w..2w+1][c] / 4).
+//   X: [nimg][H][W][C]; Y: [nimg][H/2][W/2][C]; H, W even.
+int prior_pool2_bf16(const void* X, int nimg, int H, int W, int C, void* Y, void* stream);
+
+// Decoder input: nearest x2 upsampling of the coarse level joined with the skip
+// connection along channels (exact copies):
+//   Y[n][h][w][c] = Lo[n][h/2][w/2][c] for c < C1, Skip[n][h][w][c - C1] otherwise.
+//   Lo: [nimg][H/2][W/2][C1]; Skip: [nimg][H][W][C2]; Y: [nimg][H][W][C1 + C2]; H, W even.
+int prior_upcat_bf16(const void* Lo, int C1, const void* Skip, int C2, int nimg, int H, int W, void* Y,
+                     void* stream);
+
+// Network output on the physical part of the padded grid:
+//   out[n][h][w] = scale * x[n][h][w] + D[((n*Hp + h)*Wp + w) * ldd] + bo,
+// D the FP32 result of the 1x1 output layer over the padded grid (column 0 of
+// rows of ldd floats), x and out [nimg][H][W] FP32.
+int prior_output(const float* D, int ldd, const float* x, int nimg, int H, int W, int Hp, int Wp, float scale,
+                 float bo, float* out, void* stream);
+
 // Reads and clears the internal status word (synchronises the stream).
 int prior_last_status(void* stream);
 

@@ -20,7 +20,8 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradie
            "fwi_set_kernel_variants", "fwi_kernel_variants", "fwi_chunking", "fwi_checkpoint_schedule"]
 # every symbol prior.h declares
 PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_conv3x3_wgrad_bf16", "prior_conv3x3x3_bf16",
-                 "prior_conv3x3x3_wgrad_bf16", "prior_last_status"]
+                 "prior_conv3x3x3_wgrad_bf16", "prior_last_status", "prior_first_conv_bf16", "prior_pool2_bf16",
+                 "prior_upcat_bf16", "prior_output"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -96,6 +97,14 @@ _SIGS = {
     "prior_conv3x3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, _P, _P]),
     "prior_last_status": (ctypes.c_int, [_P]),
+    "prior_first_conv_bf16": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_float, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                             _P, _P]),
+    "prior_pool2_bf16": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "prior_upcat_bf16": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _P, _P]),
+    "prior_output": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P]),
 }
 
 

@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfwi.so")
-SOURCES = ["stencil.cu", "stencil3d.cu", "aux.cu", "fwi_api.cu", "noalloc.cu", "prior.cu"]
+SOURCES = ["stencil.cu", "stencil3d.cu", "aux.cu", "fwi_api.cu", "noalloc.cu", "prior.cu", "prior_ops.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]

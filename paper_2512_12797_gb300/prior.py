@@ -49,6 +49,48 @@ def conv3x3(X, Wt, bias=None, relu=False, out_bf16=True, out=None):
     return out
 
 
+def first_conv(x, H, W, Hp, Wp, scale, sigma, Wt2, bias, relu=True):
+    """First layer: the 2-channel network input (scale * x edge-padded to
+    Hp x Wp, and sigma per image), 3x3 convolution with Wt2 [Cout][9][2] BF16
+    (prior_first_conv_bf16); returns [n, Hp, Wp, Cout] BF16."""
+    n = x.shape[0]
+    Cout = Wt2.shape[0]
+    out = torch.empty((n, Hp, Wp, Cout), dtype=torch.bfloat16, device=x.device)
+    rc = _native.lib().prior_first_conv_bf16(x.data_ptr(), n, H, W, Hp, Wp, float(scale), sigma.data_ptr(),
+                                             Wt2.data_ptr(), bias.data_ptr() if bias is not None else None, Cout,
+                                             int(relu), out.data_ptr(), _stream())
+    _check(rc, "prior_first_conv_bf16")
+    return out
+
+
+def pool2(X):
+    """2 x 2 average pooling of X [n, H, W, C] BF16 (prior_pool2_bf16)."""
+    n, H, W, C = X.shape
+    out = torch.empty((n, H // 2, W // 2, C), dtype=torch.bfloat16, device=X.device)
+    _check(_native.lib().prior_pool2_bf16(X.data_ptr(), n, H, W, C, out.data_ptr(), _stream()), "prior_pool2_bf16")
+    return out
+
+
+def upcat(lo, skip):
+    """[up2(lo), skip] along channels: lo [n, H/2, W/2, C1], skip [n, H, W, C2] (prior_upcat_bf16)."""
+    n, H, W, C2 = skip.shape
+    C1 = lo.shape[-1]
+    out = torch.empty((n, H, W, C1 + C2), dtype=torch.bfloat16, device=skip.device)
+    _check(_native.lib().prior_upcat_bf16(lo.data_ptr(), C1, skip.data_ptr(), C2, n, H, W, out.data_ptr(),
+                                          _stream()), "prior_upcat_bf16")
+    return out
+
+
+def output(D, x, Hp, Wp, scale, bo):
+    """x0-hat = scale * x + D[:, 0] + bo on the physical part [n, H, W] of the
+    padded grid (prior_output); D [n*Hp*Wp, ldd] FP32."""
+    n, H, W = x.shape
+    out = torch.empty_like(x)
+    _check(_native.lib().prior_output(D.data_ptr(), D.stride(0), x.data_ptr(), n, H, W, Hp, Wp, float(scale),
+                                      float(bo), out.data_ptr(), _stream()), "prior_output")
+    return out
+
+
 def last_status():
     """Device status word of the prior kernels (read and cleared)."""
     return _native.lib().prior_last_status(_stream())

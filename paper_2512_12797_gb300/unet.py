@@ -8,10 +8,13 @@ sigma^2 = (1 - abar_t) / abar_t, given sigma (a noise-level input map).
 
 Two evaluations of the same parameters:
   forward_torch -- plain PyTorch in FP32, used for training with autograd;
-  forward_tc    -- inference on the library's tcgen05 kernels: every 3x3
-                   convolution is prior.conv3x3 (BF16 activations, FP32
-                   accumulation) and the 1x1 output is prior.gemm_bf16;
-                   pooling, upsampling and concatenation are tensor reshapes.
+  forward_tc    -- inference on the library's kernels: every 3x3
+                   convolution but the first is prior.conv3x3 on tcgen05
+                   (BF16 activations, FP32 accumulation), the first (2 real
+                   input channels) runs on the CUDA cores with its input
+                   built on the fly, pooling and the decoder's
+                   upsample-and-join are one kernel each, and the 1x1 output
+                   is prior.gemm_bf16 plus one kernel for the skip to y.
 The network is fully convolutional; applied to a whole model it is the
 patchwise x0 prediction with overlapping patches taken to the limit (A17),
 after edge-padding to a shape the kernels tile.
@@ -79,42 +82,45 @@ def pack(p):
     wo = torch.zeros(32, 64, device=p["out.w"].device)
     wo[0] = p["out.w"].detach().float().view(64)
     q["out"] = (wo.to(torch.bfloat16).contiguous(), float(p["out.b"].detach().float().item()))
+    # the first layer's real 2 input channels, for prior_first_conv_bf16
+    q["e1a2"] = (q["e1a"][0][:, :, :2].contiguous(), q["e1a"][1])
     return q
 
 
-def _pool(h):  # NHWC average pool 2 x 2
-    n, H, W, C = h.shape
-    return h.float().view(n, H // 2, 2, W // 2, 2, C).mean((2, 4)).to(torch.bfloat16).contiguous()
-
-
-def _up(h):  # NHWC nearest upsample x 2
-    return h.repeat_interleave(2, 1).repeat_interleave(2, 2)
-
-
 def forward_tc(q, y, sigma):
-    """Inference on the tcgen05 kernels: y [n, H, W] FP32, sigma [n] -> x0-hat."""
+    """Inference on the library's kernels: y [n, H, W] FP32 (H, W tileable),
+    sigma [n] -> x0-hat."""
     n, H, W = y.shape
-    x = torch.zeros((n, H, W, 64), dtype=torch.bfloat16, device=y.device)
-    x[..., 0] = y.to(torch.bfloat16)
-    x[..., 1] = sigma.view(n, 1, 1).to(torch.bfloat16)
+    return _forward_tc(q, y, H, W, H, W, 1.0, sigma)
+
+
+def _forward_tc(q, x, H, W, Hp, Wp, scale, sigma):
+    """x0-hat of y = scale * x [n, H, W], evaluated on the grid edge-padded to
+    Hp x Wp and cropped back: the first layer builds its 2-channel input on
+    the fly (prior_first_conv_bf16), the 3x3 layers run on tcgen05, pooling
+    and the decoder's upsample-and-join are single passes (prior_pool2_bf16,
+    prior_upcat_bf16), and the 1x1 output is a tcgen05 GEMM whose result
+    prior_output adds to y on the physical grid."""
+    n = x.shape[0]
 
     def c(h, name):
         w, b = q[name]
         return TC.conv3x3(h, w, bias=b, relu=True)
 
-    h = c(x, "e1a")
+    w2, b2 = q["e1a2"]
+    h = TC.first_conv(x.contiguous(), H, W, Hp, Wp, scale, sigma.float().contiguous(), w2, b2, relu=True)
     e1 = c(h, "e1b")
-    h = c(_pool(e1), "e2a")
+    h = c(TC.pool2(e1), "e2a")
     e2 = c(h, "e2b")
-    h = c(_pool(e2), "ba")
+    h = c(TC.pool2(e2), "ba")
     h = c(h, "bb")
-    h = c(torch.cat([_up(h), e2], -1).contiguous(), "d2a")
+    h = c(TC.upcat(h, e2), "d2a")
     h = c(h, "d2b")
-    h = c(torch.cat([_up(h), e1], -1).contiguous(), "d1a")
+    h = c(TC.upcat(h, e1), "d1a")
     h = c(h, "d1b")
     wo, bo = q["out"]
-    o = TC.gemm_bf16(h.view(-1, 64), wo)[:, 0].view(n, H, W)
-    return y + o + bo
+    D = TC.gemm_bf16(h.view(-1, 64), wo)
+    return TC.output(D, x.contiguous(), Hp, Wp, scale, bo)
 
 
 def _unpool(g):  # adjoint of the 2 x 2 average pool (NHWC)
@@ -128,7 +134,9 @@ def _downsum(g):  # adjoint of the nearest x 2 upsample (NHWC)
 
 def forward_tc_train(q, y, sigma):
     """forward_tc keeping what the backward pass needs: each conv layer's input
-    and (post-ReLU) output, BF16 NHWC."""
+    and (post-ReLU) output, BF16 NHWC.  The first layer runs on tcgen05 with
+    the input's 2 channels padded to a 64-channel block, so that its weight
+    gradient can use the same kernel as the others."""
     n, H, W = y.shape
     x = torch.zeros((n, H, W, 64), dtype=torch.bfloat16, device=y.device)
     x[..., 0] = y.to(torch.bfloat16)
@@ -143,13 +151,13 @@ def forward_tc_train(q, y, sigma):
 
     h = c(x, "e1a")
     e1 = c(h, "e1b")
-    h = c(_pool(e1), "e2a")
+    h = c(TC.pool2(e1), "e2a")
     e2 = c(h, "e2b")
-    h = c(_pool(e2), "ba")
+    h = c(TC.pool2(e2), "ba")
     h = c(h, "bb")
-    h = c(torch.cat([_up(h), e2], -1).contiguous(), "d2a")
+    h = c(TC.upcat(h, e2), "d2a")
     h = c(h, "d2b")
-    h = c(torch.cat([_up(h), e1], -1).contiguous(), "d1a")
+    h = c(TC.upcat(h, e1), "d1a")
     h = c(h, "d1b")
     wo, bo = q["out"]
     o = TC.gemm_bf16(h.view(-1, 64), wo)[:, 0].view(n, H, W)
@@ -226,7 +234,7 @@ def tile_shape(H, W):
     return Hp, Wp
 
 
-def train(p, patches, steps, batch=64, lr=2e-3, sigma_range=(0.02, 3.0), seed=0, log_every=0, backend="torch"):
+def train(p, patches, steps, batch=64, lr=2e-3, sigma_range=(0.02, 3.0), seed=0, log_every=0, backend="tc"):
     """Adam on E || x0-hat(x0 + sigma eps, sigma) - x0 ||^2 with sigma
     log-uniform in sigma_range, over FP32 patches [N, S, S] on the device.
     backend "torch": PyTorch convolutions and autograd in FP32; "tc": forward
@@ -295,8 +303,6 @@ class UNetDenoiser:
 
     def __call__(self, x_t, abar_t):
         n, H, W = x_t.shape
-        y = x_t / math.sqrt(abar_t)
         sig = torch.full((n,), math.sqrt((1.0 - abar_t) / abar_t), device=x_t.device)
         Hp, Wp = tile_shape(H, W)
-        yp = F.pad(y[:, None], (0, Wp - W, 0, Hp - H), mode="replicate")[:, 0].contiguous()
-        return forward_tc(self.q, yp, sig)[:, :H, :W].contiguous()
+        return _forward_tc(self.q, x_t, H, W, Hp, Wp, 1.0 / math.sqrt(abar_t), sig)

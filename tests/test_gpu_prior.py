@@ -150,3 +150,39 @@ def test_conv3x3x3_wgrad_matches_oracle(P, n, D, H, W, Cin, Cout):
     assert _rel(dW[:, 13].cpu().double().numpy(), ref[:, 13]) < 1e-4  # centre tap
     assert _rel(dW[:, 0].cpu().double().numpy(), ref[:, 0]) < 1e-4    # corner tap
     assert P.last_status() == 0
+
+
+@pytest.mark.parametrize("n,H,W,Hp,Wp,Cout", [(2, 30, 50, 32, 64, 64), (1, 16, 16, 16, 16, 32)])
+def test_first_conv_matches_oracle(P, n, H, W, Hp, Wp, Cout):
+    # the network input built on the fly (scaled model, edge-padded to Hp x Wp,
+    # noise-level channel; both rounded to BF16) and convolved from 2 channels
+    import torch
+    g = torch.Generator().manual_seed(n * 100 + H)
+    x = torch.randn((n, H, W), generator=g) * 0.7
+    sig = torch.tensor([0.3, 1.7][:n])
+    Wt = _bf16(torch, (Cout, 9, 2), 5 + Cout)
+    bias = torch.randn(Cout, generator=g) * 0.1
+    scale = 1.25
+    Y = P.first_conv(x.cuda(), H, W, Hp, Wp, scale, sig.cuda(), Wt.cuda(), bias.cuda(), relu=True)
+    xin = np.zeros((n, Hp, Wp, 2))
+    xp = np.pad((scale * x).numpy(), ((0, 0), (0, Hp - H), (0, Wp - W)), mode="edge")
+    xin[..., 0] = torch.tensor(xp).float().to(torch.bfloat16).double().numpy()
+    xin[..., 1] = sig.to(torch.bfloat16).double().numpy()[:, None, None]
+    ref = np.maximum(PO.conv3x3(xin, Wt.float().numpy()) + bias.double().numpy(), 0.0)
+    got = Y.cpu().double().numpy()
+    # one BF16 rounding of the output on top of FP32 accumulation
+    assert _rel(got, ref) < 4e-3
+    assert np.max(np.abs(got - ref)) <= 2 ** -7 * np.max(np.abs(ref))
+
+
+def test_pool_and_upcat_layout_kernels(P):
+    import torch
+    n, H, W, C1, C2 = 2, 8, 16, 64, 32
+    X = _bf16(torch, (n, H, W, C2), 9)
+    pooled = P.pool2(X.cuda()).cpu()
+    ref = X.double().numpy().reshape(n, H // 2, 2, W // 2, 2, C2).mean(axis=(2, 4))
+    assert np.max(np.abs(pooled.double().numpy() - ref)) <= 2 ** -8 * np.max(np.abs(ref))
+    lo = _bf16(torch, (n, H // 2, W // 2, C1), 10)
+    up = P.upcat(lo.cuda(), X.cuda()).cpu()
+    assert torch.equal(up[..., :C1], lo.repeat_interleave(2, 1).repeat_interleave(2, 2))
+    assert torch.equal(up[..., C1:], X)

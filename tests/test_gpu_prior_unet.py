@@ -4,10 +4,11 @@
    same network that rounds weights and activations to BF16 at the same points
    (the remaining difference is FP32 accumulation order and, rarely, a BF16
    rounding flipped by it).
-2. Trained briefly on seeded geology patches, the network predicts the clean
-   model better than the stationary Gaussian prior's exact MMSE denoiser and
-   than no prior at all, on held-out patches, over the noise levels the
-   sampler visits.
+2. Trained briefly on seeded geology patches (with PyTorch autograd, and
+   with the library's own forward and backward kernels), the network predicts
+   the clean model better than the stationary Gaussian prior's exact MMSE
+   denoiser and than no prior at all, on held-out patches, over the noise
+   levels the sampler visits.
 """
 import math
 
@@ -52,7 +53,7 @@ def test_trained_prior_beats_gaussian_and_no_prior(U):
     from paper_2512_12797_gb300.sampler import GaussianPriorDenoiser
     train_set = torch.tensor(SP.geology_patches(8192, 64, 11)).cuda()
     p = U.init_params(0)
-    hist = U.train(p, train_set, steps=800, batch=64, lr=2e-3, seed=1, log_every=100)
+    hist = U.train(p, train_set, steps=800, batch=64, lr=2e-3, seed=1, log_every=100, backend="torch")
     assert hist[-1] < hist[0]
     held = torch.tensor(SP.geology_patches(256, 64, 99)).cuda()
     den = U.UNetDenoiser(p)
