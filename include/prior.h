@@ -51,12 +51,16 @@ int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, 
 // p = (n, y, x) and tap t = dy*3 + dx, i.e. the input's tap-shifted copies.
 //   dYt: [ceil(Cout/128)*128][P] BF16 (channel-major output gradient; rows
 //        >= Cout are read but not used); X9: [9][Cin][P] BF16;
-//   dW: [Cout][9][Cin] FP32, accumulated with atomic adds (zero it first).
-// The pixels are split into `splits` ranges per tap for parallelism; the sum
-// order therefore varies between runs.  Requires P % 64 == 0 and Cin in
+//   dW: [Cout][9][Cin] FP32, accumulated (zero it first).
+// The pixels are split into `splits` ranges per tap for parallelism.  With a
+// workspace `work` of splits * Cout * 9 * Cin floats (16-byte aligned), each
+// range stores its partial sum in its own slice and a second kernel adds the
+// slices to dW in range order: the result is the same on every run.  With
+// work = null the ranges add into dW with FP32 atomics, whose order (and so
+// the last bits) varies between runs.  Requires P % 64 == 0 and Cin in
 // {32, 64, 128, 256} or a multiple of 64.
-int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
-                             int* status, void* stream);
+int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, float* work, int P, int Cout, int Cin,
+                             int splits, int* status, void* stream);
 
 // 3D counterpart of prior_conv3x3_bf16 for volume patches (the prior of the
 // 3D models): same-size 3x3x3 cross-correlation with zero padding 1,
@@ -73,9 +77,10 @@ int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D
 // Weight gradient of prior_conv3x3x3_bf16, accumulated:
 //   dW[o][t][c] += sum_p dYt[o][p] * X27[t][c][p],
 // with X27 the input's 27 tap-shifted copies (t = dz*9 + dy*3 + dx) and the
-// other conventions of prior_conv3x3_wgrad_bf16 (splits <= 2427).
-int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, int P, int Cout, int Cin, int splits,
-                               int* status, void* stream);
+// other conventions of prior_conv3x3_wgrad_bf16 (splits <= 2427; work of
+// splits * Cout * 27 * Cin floats, or null).
+int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, float* work, int P, int Cout, int Cin,
+                               int splits, int* status, void* stream);
 
 // The memory-bound layers around the convolutions (csrc/prior_ops.cu); all
 // activations are BF16 NHWC with C a multiple of 8, pointers 16-byte aligned.

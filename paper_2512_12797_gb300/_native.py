@@ -90,11 +90,11 @@ _SIGS = {
                                        ctypes.c_int, _P, ctypes.c_int, _P, _P]),
     "prior_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
-    "prior_conv3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    "prior_conv3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, _P, _P]),
     "prior_conv3x3x3_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P]),
-    "prior_conv3x3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    "prior_conv3x3x3_wgrad_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, _P, _P]),
     "prior_last_status": (ctypes.c_int, [_P]),
     "prior_first_conv_bf16": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -177,6 +177,7 @@ struct Args {
   int Dd, TD;        // 3D convolution: depth, and planes per tile (tile = TD x TH x TW)
   int ntap;          // weight gradient: taps (9 or 27)
   int splits;        // weight gradient: pixel ranges per tap (grid z = ntap * splits)
+  float* part;       // weight gradient: per-split slices [splits][M][ldd] (plain stores), or null (atomics into D)
   int* status;
 };
 
@@ -205,10 +206,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   // K blocks of this CTA: all of K, or (weight gradient) this split's 64-pixel chunks
-  int kb0 = 0, nk = g.K / BK, tap = 0;
+  int kb0 = 0, nk = g.K / BK, tap = 0, split = 0;
   if (MODE == WGRAD) {
     tap = blockIdx.z % g.ntap;
-    const int split = blockIdx.z / g.ntap, chunks = g.K / BK;
+    split = blockIdx.z / g.ntap;
+    const int chunks = g.K / BK;
     kb0 = (int)((long long)chunks * split / g.splits);
     nk = (int)((long long)chunks * (split + 1) / g.splits) - kb0;
   }
@@ -323,7 +325,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ C
           if (g.relu) x = fmaxf(x, 0.f);
           v[i] = x;
         }
-        if (MODE == WGRAD) {
+        if (MODE == WGRAD && g.part) {  // this split's slice: plain stores, summed in order later
+          float* d = g.part + ((long long)split * g.M + row) * g.ldd + tap * g.Cin + n0 + c0;
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4*>(d + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else if (MODE == WGRAD) {
           float* d = reinterpret_cast<float*>(g.D) + (long long)row * g.ldd + tap * g.Cin + n0 + c0;
 #pragma unroll
           for (int i = 0; i < 32; i++) atomicAdd(d + i, v[i]);
@@ -496,8 +502,17 @@ int prior_conv3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int H, 
 
 namespace {
 
-int wgrad(const void* dYt, const void* Xs, float* dW, int P, int Cout, int Cin, int ntap, int splits, int* status,
-          void* stream) {
+// dW[i] += sum over s = 0 .. splits-1 of part[s][i], in that order.
+__global__ void split_sum_kernel(const float* __restrict__ part, int splits, long long n, float* dW) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float acc = dW[i];
+    for (int s = 0; s < splits; s++) acc += part[(long long)s * n + i];
+    dW[i] = acc;
+  }
+}
+
+int wgrad(const void* dYt, const void* Xs, float* dW, float* work, int P, int Cout, int Cin, int ntap, int splits,
+          int* status, void* stream) {
   const int bn = tile_n(Cin);
   const int mp = (Cout + prior::BM - 1) / prior::BM * prior::BM;
   if (!dYt || !Xs || !dW || P <= 0 || P % prior::BK || Cout <= 0 || !bn || splits < 1 || splits > 65535 / ntap)
@@ -512,6 +527,8 @@ int wgrad(const void* dYt, const void* Xs, float* dW, int P, int Cout, int Cin, 
   g.Cin = Cin;
   g.ntap = ntap;
   g.splits = splits < P / prior::BK ? splits : P / prior::BK;
+  g.part = work;
+  if (work && !aligned16(work)) return PRIOR_ERR_ARG;
   g.status = status_ptr(status);
   if (!g.status) return PRIOR_ERR_CUDA;
   CUtensorMap ma, mb;
@@ -520,16 +537,21 @@ int wgrad(const void* dYt, const void* Xs, float* dW, int P, int Cout, int Cin, 
   const cuuint64_t db[3] = {(cuuint64_t)P, (cuuint64_t)Cin, (cuuint64_t)ntap};
   const cuuint32_t bb[3] = {prior::BK, (cuuint32_t)bn, 1};
   if (!make_map(&ma, dYt, 2, da, ba) || !make_map(&mb, Xs, 3, db, bb)) return PRIOR_ERR_ARG;
-  return dispatch<prior::WGRAD>(bn, ma, mb, g, (cudaStream_t)stream);
+  const int rc = dispatch<prior::WGRAD>(bn, ma, mb, g, (cudaStream_t)stream);
+  if (rc != PRIOR_OK || !work) return rc;
+  const long long n = (long long)Cout * ntap * Cin;
+  const long long blocks = (n + 255) / 256;
+  split_sum_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(work, g.splits, n, dW);
+  return cudaGetLastError() == cudaSuccess ? PRIOR_OK : PRIOR_ERR_CUDA;
 }
 
 }  // namespace
 
 extern "C" {
 
-int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, int P, int Cout, int Cin, int splits,
-                             int* status, void* stream) {
-  return wgrad(dYt, X9, dW, P, Cout, Cin, 9, splits, status, stream);
+int prior_conv3x3_wgrad_bf16(const void* dYt, const void* X9, float* dW, float* work, int P, int Cout, int Cin,
+                             int splits, int* status, void* stream) {
+  return wgrad(dYt, X9, dW, work, P, Cout, Cin, 9, splits, status, stream);
 }
 
 int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D, int H, int W, int Cin, int Cout,
@@ -584,9 +606,9 @@ int prior_conv3x3x3_bf16(const void* X, const void* Wt, void* Y, int nimg, int D
   return dispatch<prior::CONV3>(bn, ma, mb, g, (cudaStream_t)stream);
 }
 
-int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, int P, int Cout, int Cin, int splits,
-                               int* status, void* stream) {
-  return wgrad(dYt, X27, dW, P, Cout, Cin, 27, splits, status, stream);
+int prior_conv3x3x3_wgrad_bf16(const void* dYt, const void* X27, float* dW, float* work, int P, int Cout, int Cin,
+                               int splits, int* status, void* stream) {
+  return wgrad(dYt, X27, dW, work, P, Cout, Cin, 27, splits, status, stream);
 }
 
 int prior_last_status(void* stream) {

@@ -119,9 +119,15 @@ def shifted_taps(X):
     return out
 
 
-def conv3x3_wgrad(dY, X, splits=None, out=None):
+def _sms(dev):
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def conv3x3_wgrad(dY, X, splits=None, out=None, deterministic=True):
     """Gradient of conv3x3 with respect to its weights: dW [Cout, 9, Cin] FP32
-    from the output gradient dY [n, H, W, Cout] and the input X [n, H, W, Cin]."""
+    from the output gradient dY [n, H, W, Cout] and the input X [n, H, W, Cin].
+    deterministic: per-split partial sums added in a fixed order (same result
+    on every run); else FP32 atomics."""
     n, H, W, Cout = dY.shape
     Cin = X.shape[-1]
     P = n * H * W
@@ -134,8 +140,10 @@ def conv3x3_wgrad(dY, X, splits=None, out=None):
     if splits is None:  # about two CTAs per SM over the (co, ci, tap) tiles
         bn = Cin if Cin in (32, 64, 128, 256) else (128 if Cin % 128 == 0 else 64)
         tiles = ((Cout + 127) // 128) * (Cin // bn) * 9
-        splits = max(1, min(P // 64, (2 * 152) // tiles))
-    rc = _native.lib().prior_conv3x3_wgrad_bf16(dYt.data_ptr(), X9.data_ptr(), out.data_ptr(), P, Cout, Cin,
+        splits = max(1, min(P // 64, (2 * _sms(dY.device)) // tiles))
+    work = torch.empty(splits * Cout * 9 * Cin, dtype=torch.float32, device=dY.device) if deterministic else None
+    rc = _native.lib().prior_conv3x3_wgrad_bf16(dYt.data_ptr(), X9.data_ptr(), out.data_ptr(),
+                                                work.data_ptr() if work is not None else None, P, Cout, Cin,
                                                 splits, None, _stream())
     _check(rc, "prior_conv3x3_wgrad_bf16")
     return out
@@ -178,9 +186,10 @@ def shifted_taps3(X):
     return out
 
 
-def conv3x3x3_wgrad(dY, X, splits=None, out=None):
+def conv3x3x3_wgrad(dY, X, splits=None, out=None, deterministic=True):
     """Gradient of conv3x3x3 with respect to its weights: dW [Cout, 27, Cin]
-    FP32 from the output gradient dY [n, D, H, W, Cout] and the input X."""
+    FP32 from the output gradient dY [n, D, H, W, Cout] and the input X
+    (deterministic as in conv3x3_wgrad)."""
     Cout = dY.shape[-1]
     Cin = X.shape[-1]
     P = dY.numel() // Cout
@@ -193,8 +202,10 @@ def conv3x3x3_wgrad(dY, X, splits=None, out=None):
     if splits is None:  # about two CTAs per SM over the (co, ci, tap) tiles
         bn = Cin if Cin in (32, 64, 128, 256) else (128 if Cin % 128 == 0 else 64)
         tiles = ((Cout + 127) // 128) * (Cin // bn) * 27
-        splits = max(1, min(P // 64, (2 * 152) // tiles))
-    rc = _native.lib().prior_conv3x3x3_wgrad_bf16(dYt.data_ptr(), X27.data_ptr(), out.data_ptr(), P, Cout, Cin,
+        splits = max(1, min(P // 64, (2 * _sms(dY.device)) // tiles))
+    work = torch.empty(splits * Cout * 27 * Cin, dtype=torch.float32, device=dY.device) if deterministic else None
+    rc = _native.lib().prior_conv3x3x3_wgrad_bf16(dYt.data_ptr(), X27.data_ptr(), out.data_ptr(),
+                                                  work.data_ptr() if work is not None else None, P, Cout, Cin,
                                                   splits, None, _stream())
     _check(rc, "prior_conv3x3x3_wgrad_bf16")
     return out

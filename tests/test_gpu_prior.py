@@ -99,6 +99,11 @@ def test_conv3x3_wgrad_matches_oracle(P, n, H, W, Cin, Cout):
     # the tap layout: the centre tap alone is the plain channel correlation
     assert _rel(dW[:, 4].cpu().double().numpy(), ref[:, 4]) < 1e-4
     assert P.last_status() == 0
+    # per-split partial sums added in a fixed order: the same bits on every
+    # call; the atomic form agrees to FP32 accumulation
+    assert torch.equal(P.conv3x3_wgrad(dY.cuda(), X.cuda()), dW)
+    dWa = P.conv3x3_wgrad(dY.cuda(), X.cuda(), deterministic=False)
+    assert _rel(dWa.cpu().double().numpy(), ref) < 1e-4
 
 
 # 3x3x3 convolution of volumes: the three tile forms (whole-width 128-voxel
@@ -150,6 +155,7 @@ def test_conv3x3x3_wgrad_matches_oracle(P, n, D, H, W, Cin, Cout):
     assert _rel(dW[:, 13].cpu().double().numpy(), ref[:, 13]) < 1e-4  # centre tap
     assert _rel(dW[:, 0].cpu().double().numpy(), ref[:, 0]) < 1e-4    # corner tap
     assert P.last_status() == 0
+    assert torch.equal(P.conv3x3x3_wgrad(dY.cuda(), X.cuda()), dW)
 
 
 @pytest.mark.parametrize("n,H,W,Hp,Wp,Cout", [(2, 30, 50, 32, 64, 64), (1, 16, 16, 16, 16, 32)])
