@@ -78,6 +78,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=10.0):
+        """Blocks until nvidia-smi has printed its first sample: its start-up
+        holds the driver for up to seconds, which must not fall inside the
+        timed region."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
     def stop(self):
         if self.proc is None:
             return None
@@ -258,9 +266,10 @@ def gradient_run(P, torch, w, steps, warmup, e2e_steps, dist, dev, world, rank, 
 
     def timed(fn, nsteps, it0, sampler=None):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
         if sampler:
             sampler.start()
+            sampler.wait_first()
+        barrier()
         ev0.record()
         for k in range(nsteps):
             fn(it0 + k)

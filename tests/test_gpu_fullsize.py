@@ -102,6 +102,19 @@ def test_arid_uneven_batch_sampled_parity():
     assert e_phi < 1e-5 and e_g < 1e-4 and e_d < 1e-5, (e_phi, e_g, e_d, plan)
 
 
+def test_arid_32_samples_uneven_batch_sampled_parity():
+    """The top of the near-surface workload's batch range: 32 posterior
+    samples x 8 uneven supergathers of 10 to 40 shots (256 wavefields of
+    250,881 padded points, 4000 steps) in one call, which the library
+    processes with checkpointing and, where that is cheaper, in chunks of
+    samples.  The oracle recomputes one late sample's misfit and gradient
+    (all eight supergathers) and the records of a 40-shot supergather of
+    another."""
+    w = synth.arid2d(nsamp=32)
+    e_phi, e_g, e_d, plan = _sampled_gradient_and_records(w, 27, 13, 3)
+    assert e_phi < 1e-5 and e_g < 1e-4 and e_d < 1e-5, (e_phi, e_g, e_d, plan)
+
+
 def test_layered3d_batch_sampled_records_and_directional_derivative():
     """3D layered workload at full size: 256 x 256 x 128 at 20 m, 1500 steps,
     64 sources in 4 supergathers of 16, 4096 receivers, 8 samples (32
