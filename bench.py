@@ -133,17 +133,19 @@ def job_throughput(units_per_rank, world, ms_max):
     return units_per_rank * world / (ms_max * 1e-3)
 
 
-def bytes_per_update(nsg, ndim=2):
+def bytes_per_update(nsg, ndim=2, fwd_pair=False, adj_pair=False):
     """Algorithmic HBM bytes per wavefield grid-point update of each step kernel.
 
     2D forward: read p^n, p^{n-1}, write p^{n+1} (12 B) + cc shared by the nsg
     supergathers of a sample (4/nsg B).  2D adjoint: read q^{k+1}, q^{k+2},
     p^{k-1}, write q^k (16 B) + cc and the imaging accumulator read+write
-    shared by the supergathers (12/nsg B).  3D kernels own one wavefield per
-    CTA: forward 16 B, adjoint 16 B + cc 4 B + accumulator read+write 8 B.
+    shared by the supergathers (12/nsg B).  3D kernels with one wavefield per
+    CTA: forward 16 B, adjoint 16 B + cc 4 B + accumulator read+write 8 B;
+    with pair tiles (two supergathers per CTA) cc and the accumulator are
+    shared by the pair: forward 12 + 4/2 B, adjoint 16 + 12/2 B.
     """
     if ndim == 3:
-        return {"forward": 16.0, "adjoint": 28.0}
+        return {"forward": 14.0 if fwd_pair else 16.0, "adjoint": 22.0 if adj_pair else 28.0}
     return {"forward": 12.0 + 4.0 / nsg, "adjoint": 16.0 + 12.0 / nsg}
 
 
@@ -348,7 +350,7 @@ def gradient_run(P, torch, w, steps, warmup, e2e_steps, dist, dev, world, rank, 
     # roofline of the dominant step kernel from the per-phase events.  In 2D one
     # launch runs all steps of a phase (forward: nt steps; adjoint: the steps of a
     # checkpoint segment), in 3D every step is a launch; both are charged per step.
-    bpu = bytes_per_update(nsg, w.ndim)
+    bpu = bytes_per_update(nsg, w.ndim, "pairs" in var["forward_name"], "pairs" in var["adjoint_name"])
     nchunks = (nsamp + plan["samples_per_chunk"] - 1) // plan["samples_per_chunk"]
     fwd_steps = w.nt * nchunks * steps
     rec_steps = plan["recomputed_steps"] * nchunks * steps

@@ -167,25 +167,27 @@ __global__ void source_dot_kernel(int nt, int E, const float* __restrict__ qsrc,
   if (lane == 0) tmp[(long long)b * E + e] = (float)(acc * src_amp[(long long)b * E + e]);
 }
 
-// Adds tmp into the sample's accumulator in a fixed (supergather, entry) order.
+// Adds tmp into the imaging accumulators in a fixed (supergather, entry)
+// order; wavefield b's accumulator is b / wf_per_acc (one per wavefield, per
+// pair of supergathers, or per sample).
 __global__ void source_add_kernel(int nsg, int E, const int* __restrict__ src_cnt,
                                   const long long* __restrict__ src_pos, const float* __restrict__ tmp, float* grad,
-                                  long long field, bool per_wavefield) {
+                                  long long field, int wf_per_acc) {
   const int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   for (int j = 0; j < nsg; j++) {
     const int b = s * nsg + j;
-    float* g = grad + (long long)(per_wavefield ? b : s) * field;
+    float* g = grad + (long long)(b / wf_per_acc) * field;
     for (int e = 0; e < src_cnt[b]; e++) g[src_pos[(long long)b * E + e]] += tmp[(long long)b * E + e];
   }
 }
 
 cudaError_t launch_source_imaging(int B, int nsg, int nt, int E, const float* qsrc, const float* wav,
                                   const int* src_cnt, const long long* src_pos, const float* src_amp, float* tmp,
-                                  float* grad, long long field, bool per_wavefield, cudaStream_t st) {
+                                  float* grad, long long field, int wf_per_acc, cudaStream_t st) {
   if (E <= 0) return cudaSuccess;
   source_dot_kernel<<<dim3((E + 7) / 8, B), 256, 0, st>>>(nt, E, qsrc, wav, src_cnt, src_amp, tmp);
-  source_add_kernel<<<B / nsg, 32, 0, st>>>(nsg, E, src_cnt, src_pos, tmp, grad, field, per_wavefield);
+  source_add_kernel<<<B / nsg, 32, 0, st>>>(nsg, E, src_cnt, src_pos, tmp, grad, field, wf_per_acc);
   return cudaGetLastError();
 }
 

@@ -154,6 +154,9 @@ struct fwi_ctx {
   int ns = 0, nr = 0, max_B = 0;
   std::vector<int> src_zyx, rec_zyx;  // padded coordinates
   int ntx = 0, ntz = 0, nty = 1, ntiles = 0;
+  // tiles per tile shape: [0] the 2D tile or the 3D 64 x 16 tile, [1] the 3D
+  // 64 x 8 pair tile (two supergathers per CTA); ntiles == ntiles_s[0]
+  int ntiles_s[2] = {0, 0};
   double cell_volume = 1.0, vmax_cfl = 0.0;
 
   // device memory
@@ -170,10 +173,11 @@ struct fwi_ctx {
   int* status = nullptr;
   int nblk = 0, Emax = 0;
   // receiver lists (shared by all wavefields): forward sampling, adjoint injection
-  int* rec_off = nullptr;
-  int2* rec_smp = nullptr;   // 2D sampling entries
-  int4* rec_smp4 = nullptr;  // 3D sampling entries (z in .z)
-  int4* rec_inj = nullptr;   // adjoint injection entries (z in .w)
+  // per tile shape
+  int* rec_off[2] = {};
+  int2* rec_smp = nullptr;      // 2D sampling entries
+  int4* rec_smp4[2] = {};       // 3D sampling entries (z in .z)
+  int4* rec_inj[2] = {};        // adjoint injection entries (z in .w)
   // per-call lists
   unsigned char* dlist = nullptr;
   unsigned char* hlist[kStaging] = {};  // pinned staging, used in turn
@@ -192,7 +196,8 @@ struct fwi_ctx {
   // step-kernel variants: chosen per call shape by timing (autotune), or forced
   int var[2] = {-1, -1};
   int forced[2] = {-1, -1};
-  int tuned_B = -1;
+  int tuned_B = -1, tuned_nsg = -1;  // call shape the variants were tuned for
+  int adj_pair = 0;  // tile shape of the 3D adjoint in the last tuned call (shape_adj)
   float tune_ms[2][8] = {};
   int* zero_off = nullptr;  // [ntiles+1] zeros: "no points in any tile"
   float* gtab = nullptr;    // gamma*dt per axis: z [nzp], y [nyp], x [nxp]
@@ -255,38 +260,44 @@ Coef make_coef(const fwi_grid* g) {
   return K;
 }
 
+// Rows of a 3D wavefield tile for tile shape sh: 64 x 16, or 64 x 8 (pair tiles).
+inline int tile_rows3(int sh) { return sh ? TY3 / 2 : TY3; }
+
 // Tile of padded point (z, y, x) and its local index inside the tile.
-// 2D tiles are 128 (x) x 32 (z); 3D tiles are 64 (x) x 16 (y) columns in z.
-void tile_of(const fwi_ctx* C, const Entry& e, int* tile, int* local) {
+// 2D tiles are 128 (x) x 32 (z); 3D tiles are 64 (x) x 16 or 64 x 8 (y) columns in z.
+void tile_of(const fwi_ctx* C, const Entry& e, int sh, int* tile, int* local) {
   if (C->L.ndim == 3) {
-    *tile = (e.y / TY3) * C->ntx + e.x / TX3;
-    *local = (e.y % TY3) * TX3 + (e.x % TX3);
+    const int ty = tile_rows3(sh);
+    *tile = (e.y / ty) * C->ntx + e.x / TX3;
+    *local = (e.y % ty) * TX3 + (e.x % TX3);
   } else {
     *tile = (e.z / TZ) * C->ntx + e.x / TX;
     *local = (e.z % TZ) * TX + (e.x % TX);
   }
 }
 
-// Builds CSR offsets [nb_lists][ntiles+1] and entries for lists of points.
+// Builds CSR offsets [nb_lists][ntiles+1] and entries for lists of points
+// under tile shape sh.
 template <typename Fill>
-void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, int* off, Fill fill) {
+void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, int sh, int* off, Fill fill) {
   int pos = 0;
+  const int nt = C->ntiles_s[sh];
   for (size_t b = 0; b < lists.size(); b++) {
     std::vector<std::pair<long long, int>> order;  // ((tile, z), index)
     for (size_t i = 0; i < lists[b].size(); i++) {
       int t, l;
-      tile_of(C, lists[b][i], &t, &l);
+      tile_of(C, lists[b][i], sh, &t, &l);
       order.push_back({(long long)t * (1LL << 32) + lists[b][i].z, (int)i});
     }
     std::stable_sort(order.begin(), order.end());
     size_t k = 0;
-    for (int t = 0; t <= C->ntiles; t++) {
-      off[b * (C->ntiles + 1) + t] = pos;
-      if (t == C->ntiles) break;
+    for (int t = 0; t <= nt; t++) {
+      off[b * (nt + 1) + t] = pos;
+      if (t == nt) break;
       while (k < order.size() && (order[k].first >> 32) == t) {
         const Entry& e = lists[b][order[k].second];
         int tt, l;
-        tile_of(C, e, &tt, &l);
+        tile_of(C, e, sh, &tt, &l);
         fill(pos, l, e);
         pos++;
         k++;
@@ -295,59 +306,55 @@ void build_csr(const fwi_ctx* C, const std::vector<std::vector<Entry>>& lists, i
   }
 }
 
-int make_tmaps(fwi_ctx* C, int B, int nslots, CUtensorMap* halo, CUtensorMap* plain, CUtensorMap* ctile,
-               CUtensorMap* gtile) {
+// TMA descriptors of a call, per tile shape: the stepped level's halo tile,
+// the plain tile of the older level, the cc tile and (3D) the imaging
+// accumulator tile.  2D uses shape 0 only.
+struct Maps {
+  CUtensorMap th[2], tp[2], tc[2], tg[2];
+};
+
+int make_tmaps(fwi_ctx* C, int B, int nslots, Maps* M) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return FWI_ERR_CUDA;
   const Layout& L = C->L;
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  auto encode = [&](CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* str,
+                    const cuuint32_t* box) {
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, str, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
   if (L.ndim == 2) {
     const cuuint64_t dims[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)B, (cuuint64_t)nslots};
     const cuuint64_t str[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NZ * 4, (cuuint64_t)L.field * B * 4};
     const cuuint32_t bh[4] = {HX, HZ, 1, 1}, bp[4] = {TX, TZ, 1, 1};
-    if (enc(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->pool, dims, str, bh, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return FWI_ERR_CUDA;
-    if (enc(plain, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->pool, dims, str, bp, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return FWI_ERR_CUDA;
     const cuuint64_t cd[3] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
     const cuuint64_t cs[2] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.field * 4};
     const cuuint32_t cb[3] = {TX, TZ, 1};
-    if (enc(ctile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, C->c, cd, cs, cb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (!encode(&M->th[0], 4, C->pool, dims, str, bh) || !encode(&M->tp[0], 4, C->pool, dims, str, bp) ||
+        !encode(&M->tc[0], 3, C->c, cd, cs, cb))
       return FWI_ERR_CUDA;
-    *gtile = *ctile;  // unused by the 2D kernels
+    M->tg[0] = M->tc[0];  // unused by the 2D kernels
+    M->th[1] = M->th[0];
+    M->tp[1] = M->tp[0];
+    M->tc[1] = M->tc[0];
+    M->tg[1] = M->tg[0];
     return FWI_OK;
   }
   const cuuint64_t dims[5] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)B,
                               (cuuint64_t)nslots};
   const cuuint64_t str[4] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4,
                              (cuuint64_t)L.field * B * 4};
-  const cuuint32_t bh[5] = {HX3, TY3 + 2 * HALO, 1, 1, 1}, bp[5] = {TX3, TY3, 1, 1, 1};
-  if (enc(halo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, C->pool, dims, str, bh, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return FWI_ERR_CUDA;
-  if (enc(plain, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, C->pool, dims, str, bp, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return FWI_ERR_CUDA;
-  // cc per sample and the imaging accumulator per wavefield, plain planes
+  // cc per sample and the imaging accumulators (per wavefield or per pair), plain planes
   const cuuint64_t d4[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
   const cuuint64_t s4[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NY * 4, (cuuint64_t)L.field * 4};
-  const cuuint32_t b4[4] = {TX3, TY3, 1, 1};
-  if (enc(ctile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->c, d4, s4, b4, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return FWI_ERR_CUDA;
-  if (enc(gtile, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C->G, d4, s4, b4, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return FWI_ERR_CUDA;
+  for (int sh = 0; sh < 2; sh++) {
+    const cuuint32_t ty = (cuuint32_t)tile_rows3(sh);
+    const cuuint32_t bh[5] = {HX3, ty + 2 * HALO, 1, 1, 1}, bp[5] = {TX3, ty, 1, 1, 1}, b4[4] = {TX3, ty, 1, 1};
+    if (!encode(&M->th[sh], 5, C->pool, dims, str, bh) || !encode(&M->tp[sh], 5, C->pool, dims, str, bp) ||
+        !encode(&M->tc[sh], 4, C->c, d4, s4, b4) || !encode(&M->tg[sh], 4, C->G, d4, s4, b4))
+      return FWI_ERR_CUDA;
+  }
   return FWI_OK;
 }
 
@@ -363,8 +370,8 @@ int partition_pool(fwi_ctx* C, int B, cudaStream_t st, long long* nslots) {
   return FWI_OK;
 }
 
-struct CallLists {  // byte offsets into the per-call list buffer
-  size_t inj_off, inj, smp_off, smp, shot_off, shot_id, shot_w, src_cnt, src_pos, src_amp, total;
+struct CallLists {  // byte offsets into the per-call list buffer; tile CSR lists per tile shape
+  size_t inj_off[2], inj[2], smp_off[2], smp[2], shot_off, shot_id, shot_w, src_cnt, src_pos, src_amp, total;
 };
 
 // Per-call lists from the encoding: merged source points per wavefield (forward
@@ -411,10 +418,21 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
     p = (p + bytes + 255) / 256 * 256;
     return r;
   };
-  cl->inj_off = take((size_t)B * (C->ntiles + 1) * 4);
-  cl->inj = take((size_t)std::max(nent, 1) * 16);
-  cl->smp_off = take((size_t)B * (C->ntiles + 1) * 4);
-  cl->smp = take((size_t)std::max(nent, 1) * 16);
+  const int nsh = C->L.ndim == 3 ? 2 : 1;
+  for (int sh = 0; sh < 2; sh++) {
+    const int sh_eff = sh < nsh ? sh : 0;  // 2D: shape 1 aliases shape 0
+    if (sh != sh_eff) {
+      cl->inj_off[sh] = cl->inj_off[0];
+      cl->inj[sh] = cl->inj[0];
+      cl->smp_off[sh] = cl->smp_off[0];
+      cl->smp[sh] = cl->smp[0];
+      continue;
+    }
+    cl->inj_off[sh] = take((size_t)B * (C->ntiles_s[sh] + 1) * 4);
+    cl->inj[sh] = take((size_t)std::max(nent, 1) * 16);
+    cl->smp_off[sh] = take((size_t)B * (C->ntiles_s[sh] + 1) * 4);
+    cl->smp[sh] = take((size_t)std::max(nent, 1) * 16);
+  }
   cl->shot_off = take((size_t)(B + 1) * 4);
   cl->shot_id = take((size_t)std::max(nshot, 1) * 4);
   cl->shot_w = take((size_t)std::max(nshot, 1) * 4);
@@ -430,22 +448,24 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
   CK(cudaEventSynchronize(C->ev_list[turn]));
   unsigned char* h = C->hlist[turn];
   const float inv_vol = (float)(1.0 / C->cell_volume);
-  build_csr(C, lists, reinterpret_cast<int*>(h + cl->inj_off), [&](int pos, int local, const Entry& e) {
-    int4 v;
-    v.x = local;
-    v.y = 0;
-    float a = e.amp * inv_vol;
-    memcpy(&v.z, &a, 4);
-    v.w = e.z;
-    reinterpret_cast<int4*>(h + cl->inj)[pos] = v;
-  });
   const bool is3d = C->L.ndim == 3;
-  build_csr(C, lists, reinterpret_cast<int*>(h + cl->smp_off), [&](int pos, int local, const Entry& e) {
-    if (is3d)
-      reinterpret_cast<int4*>(h + cl->smp)[pos] = make_int4(local, e.col, e.z, 0);
-    else
-      reinterpret_cast<int2*>(h + cl->smp)[pos] = make_int2(local, e.col);
-  });
+  for (int sh = 0; sh < nsh; sh++) {
+    build_csr(C, lists, sh, reinterpret_cast<int*>(h + cl->inj_off[sh]), [&](int pos, int local, const Entry& e) {
+      int4 v;
+      v.x = local;
+      v.y = 0;
+      float a = e.amp * inv_vol;
+      memcpy(&v.z, &a, 4);
+      v.w = e.z;
+      reinterpret_cast<int4*>(h + cl->inj[sh])[pos] = v;
+    });
+    build_csr(C, lists, sh, reinterpret_cast<int*>(h + cl->smp_off[sh]), [&](int pos, int local, const Entry& e) {
+      if (is3d)
+        reinterpret_cast<int4*>(h + cl->smp[sh])[pos] = make_int4(local, e.col, e.z, 0);
+      else
+        reinterpret_cast<int2*>(h + cl->smp[sh])[pos] = make_int2(local, e.col);
+    });
+  }
   int* so = reinterpret_cast<int*>(h + cl->shot_off);
   int* sid = reinterpret_cast<int*>(h + cl->shot_id);
   float* sw = reinterpret_cast<float*>(h + cl->shot_w);
@@ -489,7 +509,14 @@ int validate_call(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, 
   return FWI_OK;
 }
 
-StepParams base_params(fwi_ctx* C, int B, int nsg) {
+// 3D tile shape of the forward kernel (the autotuned variant's bit 2) and of
+// the adjoint kernel (by rule: pair tiles whenever a sample has an even
+// number of supergathers, since the pair form sums the imaging term in
+// another order); 2D has one shape.
+int shape_fwd(const fwi_ctx* C) { return C->L.ndim == 3 ? (C->var[0] >> 2) & 1 : 0; }
+int shape_adj(const fwi_ctx* C, int nsg) { return C->L.ndim == 3 && nsg % 2 == 0 ? 1 : 0; }
+
+StepParams base_params(fwi_ctx* C, int B, int nsg, int sh = 0) {
   StepParams P;
   memset(&P, 0, sizeof(P));
   P.pool = C->pool;
@@ -501,17 +528,19 @@ StepParams base_params(fwi_ctx* C, int B, int nsg) {
   P.smp_bstride = 0;
   P.nsg = nsg;
   P.ntx = C->ntx;
-  P.ntiles = C->ntiles;
+  P.ntiles = C->ntiles_s[sh];
+  P.pair3 = sh;
   P.status = C->status;
   return P;
 }
 
 // Steps descs[off, off + n) of the current call: one multi-step launch in 2D
 // (progress flags zeroed first), one launch per step in 3D.
-int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int B, const CUtensorMap& th,
-              const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, cudaStream_t st,
+// P carries its tile shape (P.pair3) and that shape's lists.
+int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int B, const Maps& M, cudaStream_t st,
               long long* launches) {
   if (n <= 0) return FWI_OK;
+  const int sh = P.pair3;
   if (C->L.ndim == 3) {
     for (int i = 0; i < n; i++) {
       const StepDesc& d = C->descs[off + i];
@@ -521,8 +550,8 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
       P.s_snap = d.snap;
       P.t = d.t;
       P.order3 = C->var[adj ? 1 : 0] & 1;
-      P.zpair3 = C->var[adj ? 1 : 0] >> 1;
-      CK(launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st));
+      P.zpair3 = (C->var[adj ? 1 : 0] >> 1) & 1;
+      CK(launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st));
     }
     *launches += n;
     return FWI_OK;
@@ -531,7 +560,7 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
   P.nsteps = n;
   P.done = C->done;
   CK(cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st));
-  CK(launch_step2d(adj, C->var[adj ? 1 : 0], th, tp, tc, C->L, C->K, P, nsamp, st));
+  CK(launch_step2d(adj, C->var[adj ? 1 : 0], M.th[0], M.tp[0], M.tc[0], C->L, C->K, P, nsamp, st));
   *launches += 1;
   return FWI_OK;
 }
@@ -560,40 +589,49 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
   return d;
 }
 
-// Step-kernel variants: 2D ring depths (stencil.cu); 3D CTA orders.
-// 3D variant v: bit 0 the CTA order, bit 1 two z levels per march step.
-int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 4 : num_variants2d(adj); }
+// Step-kernel variants: 2D ring depths (stencil.cu).  3D variant v: bit 0
+// the CTA order (tile-major, wavefield-fastest), bit 1 two z levels per march
+// step, and for the forward bit 2 the tile shape (64 x 16, or 64 x 8 pair
+// tiles, offered when a sample has an even number of supergathers).  The 3D
+// adjoint's tile shape follows shape_adj.
+int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? (adj ? 4 : 8) : num_variants2d(adj); }
 const char* variant_name(const fwi_ctx* C, bool adj, int v) {
   if (C->L.ndim == 2) return variant2d_name(adj, v);
-  static const char* names[2][4] = {
-      {"fwd3d tile-major, 1 level", "fwd3d wavefield-fastest, 1 level", "fwd3d tile-major, 2 levels",
-       "fwd3d wavefield-fastest, 2 levels"},
-      {"adj3d tile-major, 1 level", "adj3d wavefield-fastest, 1 level", "adj3d tile-major, 2 levels",
-       "adj3d wavefield-fastest, 2 levels"}};
-  return v < 0 || v > 3 ? "-" : names[adj ? 1 : 0][v];
+  static const char* fwd[8] = {
+      "fwd3d 64x16 tile-major, 1 level", "fwd3d 64x16 wavefield-fastest, 1 level",
+      "fwd3d 64x16 tile-major, 2 levels", "fwd3d 64x16 wavefield-fastest, 2 levels",
+      "fwd3d 64x8 pairs tile-major, 1 level", "fwd3d 64x8 pairs wavefield-fastest, 1 level",
+      "fwd3d 64x8 pairs tile-major, 2 levels", "fwd3d 64x8 pairs wavefield-fastest, 2 levels"};
+  static const char* adjn[2][4] = {
+      {"adj3d 64x16 tile-major, 1 level", "adj3d 64x16 wavefield-fastest, 1 level",
+       "adj3d 64x16 tile-major, 2 levels", "adj3d 64x16 wavefield-fastest, 2 levels"},
+      {"adj3d 64x8 pairs tile-major, 1 level", "adj3d 64x8 pairs wavefield-fastest, 1 level",
+       "adj3d 64x8 pairs tile-major, 2 levels", "adj3d 64x8 pairs wavefield-fastest, 2 levels"}};
+  if (v < 0) return "-";
+  return adj ? (v < 4 ? adjn[C->adj_pair][v] : "-") : (v < 8 ? fwd[v] : "-");
 }
 
 // kTuneSteps steps of variant v: one multi-step launch in 2D, one launch per
-// step in 3D (slots from td).
+// step in 3D (slots from td).  P carries the variant's tile shape and lists.
 cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDesc* td, int nsamp, int B,
-                        const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg,
-                        cudaStream_t st) {
+                        const Maps& M, cudaStream_t st) {
   if (C->L.ndim == 3) {
     P.order3 = v & 1;
-    P.zpair3 = v >> 1;
+    P.zpair3 = (v >> 1) & 1;
+    const int sh = P.pair3;
     for (int i = 0; i < kTuneSteps; i++) {
       P.s_cur = td[i].cur;
       P.s_prev = td[i].prev;
       P.s_out = td[i].out;
       P.s_snap = td[i].snap;
-      cudaError_t e = launch_step3d(adj, th, tp, tc, tg, C->L, C->K, P, B, st);
+      cudaError_t e = launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
   cudaError_t e = cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st);
   if (e != cudaSuccess) return e;
-  return launch_step2d(adj, v, th, tp, tc, C->L, C->K, P, nsamp, st);
+  return launch_step2d(adj, v, M.th[0], M.tp[0], M.tc[0], C->L, C->K, P, nsamp, st);
 }
 
 // Autotuner: time every variant of the forward and adjoint step kernels on
@@ -601,11 +639,11 @@ cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDes
 // slots hold, no injection or sampling) and keep the fastest.  Runs once per
 // wavefield count; synchronises the stream while it times.  All variants give
 // bit-identical results.  The 3D adjoint variant writes the imaging
-// accumulator, which every gradient chunk clears after tuning.
-int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
-             const CUtensorMap& tg, long long nslots, cudaStream_t st) {
+// accumulators, which every gradient chunk clears after tuning.
+int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cudaStream_t st) {
   const int B = nsamp * nsg;
-  if (C->tuned_B == B && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
+  C->adj_pair = shape_adj(C, nsg);
+  if (C->tuned_B == B && C->tuned_nsg == nsg && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
   // timing steps with the traffic of real ones: the three ring slots rotate
   // (whatever they hold), the snapshot comes from a fourth slot when there is one
   StepDesc td[kTuneSteps];
@@ -619,28 +657,33 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtens
   CK(cudaEventCreate(&e1));
   for (int adj = 0; adj < 2; adj++) {
     const int nv = num_variants(C, adj != 0);
+    for (int v = 0; v < 8; v++) C->tune_ms[adj][v] = -1.f;
     if (C->forced[adj] >= 0 && C->forced[adj] < nv) {
-      C->var[adj] = C->forced[adj];
+      // a forced 3D pair-tile forward needs an even number of supergathers:
+      // otherwise the same variant with 64 x 16 tiles
+      C->var[adj] = (C->L.ndim == 3 && !adj && nsg % 2) ? (C->forced[adj] & 3) : C->forced[adj];
       continue;
     }
-    StepParams P = base_params(C, B, nsg);
-    P.inj_off = C->zero_off;
-    P.inj_bstride = 0;
-    P.inj = C->rec_inj;
-    P.series = C->wav;
-    P.steps = C->tdesc;
-    P.nsteps = kTuneSteps;
-    P.done = C->done;
     int best = -1;
     float best_ms = 1e30f;
     for (int v = 0; v < nv && v < 8; v++) {
-      C->tune_ms[adj][v] = -1.f;
-      if (launch_tune(C, adj != 0, v, P, td, nsamp, B, th, tp, tc, tg, st) != cudaSuccess) {
+      // pair tiles need an even number of supergathers per sample
+      const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : 0;
+      if (sh && nsg % 2) continue;
+      StepParams P = base_params(C, B, nsg, sh);
+      P.inj_off = C->zero_off;
+      P.inj_bstride = 0;
+      P.inj = C->rec_inj[sh];
+      P.series = C->wav;
+      P.steps = C->tdesc;
+      P.nsteps = kTuneSteps;
+      P.done = C->done;
+      if (launch_tune(C, adj != 0, v, P, td, nsamp, B, M, st) != cudaSuccess) {
         cudaGetLastError();  // variant does not fit this device: skip it
         continue;
       }
       CK(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; r++) CK(launch_tune(C, adj != 0, v, P, td, nsamp, B, th, tp, tc, tg, st));
+      for (int r = 0; r < 3; r++) CK(launch_tune(C, adj != 0, v, P, td, nsamp, B, M, st));
       CK(cudaEventRecord(e1, st));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -657,6 +700,7 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const CUtensorMap& th, const CUtens
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   C->tuned_B = B;
+  C->tuned_nsg = nsg;
   return FWI_OK;
 }
 
@@ -744,6 +788,8 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
   C->ntz = (L.nzp + TZ - 1) / TZ;
   C->nty = (L.nyp + TY3 - 1) / TY3;
   C->ntiles = C->ntx * (g->ndim == 3 ? C->nty : C->ntz);
+  C->ntiles_s[0] = C->ntiles;
+  C->ntiles_s[1] = g->ndim == 3 ? C->ntx * ((L.nyp + tile_rows3(1) - 1) / tile_rows3(1)) : 0;
   C->Emax = std::min(C->ns, 4096);
   C->nblk = 64;
 
@@ -759,15 +805,15 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
-  // receiver lists, shared by every wavefield
-  {
+  // receiver lists, shared by every wavefield, per tile shape
+  for (int sh = 0; sh < (g->ndim == 3 ? 2 : 1); sh++) {
     std::vector<std::vector<Entry>> rl(1);
     for (int r = 0; r < C->nr; r++) rl[0].push_back({C->rec_zyx[3 * r], C->rec_zyx[3 * r + 1], C->rec_zyx[3 * r + 2], r, 1.f});
-    std::vector<int> off(C->ntiles + 1);
+    std::vector<int> off(C->ntiles_s[sh] + 1);
     std::vector<int2> smp(C->nr);
     std::vector<int4> smp4(C->nr);
     std::vector<int4> inj(C->nr);
-    build_csr(C, rl, off.data(), [&](int pos, int local, const Entry& e) {
+    build_csr(C, rl, sh, off.data(), [&](int pos, int local, const Entry& e) {
       smp[pos] = make_int2(local, e.col);
       smp4[pos] = make_int4(local, e.col, e.z, 0);
       int4 v;
@@ -778,21 +824,27 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
       v.w = e.z;
       inj[pos] = v;
     });
-    if (!alloc((void**)&C->rec_off, off.size() * 4) || !alloc((void**)&C->rec_smp, smp.size() * 8) ||
-        !alloc((void**)&C->rec_smp4, smp4.size() * 16) || !alloc((void**)&C->rec_inj, inj.size() * 16)) {
+    if (!alloc((void**)&C->rec_off[sh], off.size() * 4) || (sh == 0 && !alloc((void**)&C->rec_smp, smp.size() * 8)) ||
+        !alloc((void**)&C->rec_smp4[sh], smp4.size() * 16) || !alloc((void**)&C->rec_inj[sh], inj.size() * 16)) {
       fwi_destroy(C);
       return FWI_ERR_OOM;
     }
-    if (cudaMemcpy(C->rec_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(C->rec_smp, smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(C->rec_smp4, smp4.data(), smp4.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(C->rec_inj, inj.data(), inj.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(C->rec_off[sh], off.data(), off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (sh == 0 && cudaMemcpy(C->rec_smp, smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(C->rec_smp4[sh], smp4.data(), smp4.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(C->rec_inj[sh], inj.data(), inj.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
       fwi_destroy(C);
       return FWI_ERR_CUDA;
     }
   }
-  if (!alloc((void**)&C->zero_off, (size_t)(C->ntiles + 1) * 4) ||
-      cudaMemset(C->zero_off, 0, (size_t)(C->ntiles + 1) * 4) != cudaSuccess) {
+  if (g->ndim == 2) {  // one tile shape: shape 1 aliases shape 0
+    C->rec_off[1] = C->rec_off[0];
+    C->rec_smp4[1] = C->rec_smp4[0];
+    C->rec_inj[1] = C->rec_inj[0];
+  }
+  const int ntiles_max = std::max(C->ntiles_s[0], C->ntiles_s[1]);
+  if (!alloc((void**)&C->zero_off, (size_t)(ntiles_max + 1) * 4) ||
+      cudaMemset(C->zero_off, 0, (size_t)(ntiles_max + 1) * 4) != cudaSuccess) {
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
@@ -818,7 +870,8 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     }
   }
   // per-call list buffers (worst case: every shot its own node)
-  C->list_bytes = (size_t)B * (C->ntiles + 1) * 8 + (size_t)B * C->Emax * (16 + 16 + 8 + 4) +
+  // (3D: the tile CSR lists of both tile shapes)
+  C->list_bytes = (size_t)B * (C->ntiles_s[0] + C->ntiles_s[1] + 2) * 8 + (size_t)B * C->Emax * (2 * 32 + 8 + 4) +
                   (size_t)(B + 1) * 4 + (size_t)B * C->ns * 8 + (size_t)B * 4 + 64 * 256;
   if (!alloc((void**)&C->dlist, C->list_bytes) ||
       [&] {
@@ -895,10 +948,12 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->qsrc);
   cudaFree(C->stmp);
   cudaFree(C->status);
-  cudaFree(C->rec_off);
+  for (int sh = 0; sh < (C->L.ndim == 3 ? 2 : 1); sh++) {
+    cudaFree(C->rec_off[sh]);
+    cudaFree(C->rec_smp4[sh]);
+    cudaFree(C->rec_inj[sh]);
+  }
   cudaFree(C->rec_smp);
-  cudaFree(C->rec_smp4);
-  cudaFree(C->rec_inj);
   cudaFree(C->dlist);
   cudaFree(C->zero_off);
   cudaFree(C->gtab);
@@ -950,27 +1005,27 @@ static void gradient_descs(const Plan& plan, int nt, std::vector<StepDesc>& desc
   }
 }
 
-static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const CUtensorMap& th,
-                            const CUtensorMap& tp, const CUtensorMap& tc, const CUtensorMap& tg, int desc_off,
+static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl, const Maps& M, int desc_off,
                             float* dout, cudaStream_t st) {
   const int B = nsamp * nsg;
-  StepParams P = base_params(C, B, nsg);
-  P.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
-  P.inj_bstride = C->ntiles + 1;
-  P.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj);
+  const int sh = shape_fwd(C);
+  StepParams P = base_params(C, B, nsg, sh);
+  P.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off[sh]);
+  P.inj_bstride = C->ntiles_s[sh] + 1;
+  P.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj[sh]);
   P.series = C->wav;
   P.series_bstride = 0;
   P.series_ld = 1;
-  P.smp_off = C->rec_off;
+  P.smp_off = C->rec_off[sh];
   P.smp_bstride = 0;
   if (C->L.ndim == 3)
-    P.smp4 = C->rec_smp4;
+    P.smp4 = C->rec_smp4[sh];
   else
     P.smp = C->rec_smp;
   P.smp_out = dout;
   P.smp_bstride_out = (long long)C->g.nt * C->nr;
   P.smp_ld = C->nr;
-  return run_steps(C, false, P, desc_off, C->g.nt, nsamp, B, th, tp, tc, tg, st, &C->launches[0]);
+  return run_steps(C, false, P, desc_off, C->g.nt, nsamp, B, M, st, &C->launches[0]);
 }
 
 int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, const int8_t* w, const int32_t* sg,
@@ -984,9 +1039,9 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   long long nslots;
   if ((rc = partition_pool(C, B, st, &nslots)) != FWI_OK) return rc;
   if (nslots < 4) return FWI_ERR_OOM;
-  CUtensorMap th, tp, tc, tg;
-  if ((rc = make_tmaps(C, B, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, nsamp, nsg, th, tp, tc, tg, nslots, st)) != FWI_OK) return rc;
+  Maps M;
+  if ((rc = make_tmaps(C, B, (int)nslots, &M)) != FWI_OK) return rc;
+  if ((rc = autotune(C, nsamp, nsg, M, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
@@ -997,7 +1052,7 @@ int fwi_forward(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, co
   append_forward_descs(C);
   if ((rc = upload_descs(C, st)) != FWI_OK) return rc;
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, d_pred, st)) != FWI_OK) return rc;
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, M, 0, d_pred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
   prof_mark(C, 2, st);
   prof_mark(C, 3, st);
@@ -1023,9 +1078,9 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   if (!make_plan(nt, nslots, &plan)) return FWI_ERR_OOM;
   C->plan = plan;
   C->slots_avail = nslots;
-  CUtensorMap th, tp, tc, tg;
-  if ((rc = make_tmaps(C, Bpart, (int)nslots, &th, &tp, &tc, &tg)) != FWI_OK) return rc;
-  if ((rc = autotune(C, Bpart / nsg, nsg, th, tp, tc, tg, nslots, st)) != FWI_OK) return rc;
+  Maps M;
+  if ((rc = make_tmaps(C, Bpart, (int)nslots, &M)) != FWI_OK) return rc;
+  if ((rc = autotune(C, Bpart / nsg, nsg, M, nslots, st)) != FWI_OK) return rc;
   CallLists cl;
   int Emax;
   if ((rc = build_call_lists(C, nsamp, perm, w, sg, nsg, &cl, &Emax, st)) != FWI_OK) return rc;
@@ -1039,9 +1094,12 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
 
   CK(launch_expand(C->L, vel, nsamp, C->g.dt, C->gtab, C->c, (float)C->vmax_cfl, C->status, st));
   C->launches[0] += 1;
-  const bool g_per_wf = C->L.ndim == 3;  // 3D: one imaging accumulator per wavefield
-  CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (g_per_wf ? B : nsamp) * 4, st));
-  if ((rc = run_forward_loop(C, nsamp, nsg, cl, th, tp, tc, tg, 0, C->dpred, st)) != FWI_OK) return rc;
+  // imaging accumulators: one per sample (2D), per pair of supergathers (3D
+  // pair tiles) or per wavefield (3D)
+  const int sh_a = shape_adj(C, nsg);
+  const int wf_per_acc = C->L.ndim == 2 ? nsg : (sh_a ? 2 : 1);
+  CK(cudaMemsetAsync(C->G, 0, (size_t)C->L.field * (B / wf_per_acc) * 4, st));
+  if ((rc = run_forward_loop(C, nsamp, nsg, cl, M, 0, C->dpred, st)) != FWI_OK) return rc;
   prof_mark(C, 1, st);
 
   nv.phase(cot ? "cotangent" : "residual and misfit");
@@ -1060,34 +1118,33 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
 
   nv.phase("reverse sweep");
   // reverse sweep: recompute each earlier segment, then the adjoint steps
-  StepParams F = base_params(C, B, nsg);  // recompute: sources only, no sampling
-  F.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off);
-  F.inj_bstride = C->ntiles + 1;
-  F.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj);
+  const int sh_f = shape_fwd(C);
+  StepParams F = base_params(C, B, nsg, sh_f);  // recompute: sources only, no sampling
+  F.inj_off = reinterpret_cast<const int*>(C->dlist + cl.inj_off[sh_f]);
+  F.inj_bstride = C->ntiles_s[sh_f] + 1;
+  F.inj = reinterpret_cast<const int4*>(C->dlist + cl.inj[sh_f]);
   F.series = C->wav;
   F.series_ld = 1;
-  StepParams A = base_params(C, B, nsg);  // adjoint: residual at receivers, sample sources
-  A.inj_off = C->rec_off;
+  StepParams A = base_params(C, B, nsg, sh_a);  // adjoint: residual at receivers, sample sources
+  A.inj_off = C->rec_off[sh_a];
   A.inj_bstride = 0;
-  A.inj = C->rec_inj;
+  A.inj = C->rec_inj[sh_a];
   A.series = C->dpred;
   A.series_bstride = (long long)nt * nr;
   A.series_ld = nr;
-  A.smp_off = reinterpret_cast<const int*>(C->dlist + cl.smp_off);
-  A.smp_bstride = C->ntiles + 1;
+  A.smp_off = reinterpret_cast<const int*>(C->dlist + cl.smp_off[sh_a]);
+  A.smp_bstride = C->ntiles_s[sh_a] + 1;
   if (C->L.ndim == 3)
-    A.smp4 = reinterpret_cast<const int4*>(C->dlist + cl.smp);
+    A.smp4 = reinterpret_cast<const int4*>(C->dlist + cl.smp[sh_a]);
   else
-    A.smp = reinterpret_cast<const int2*>(C->dlist + cl.smp);
+    A.smp = reinterpret_cast<const int2*>(C->dlist + cl.smp[sh_a]);
   A.smp_out = C->qsrc;
   A.smp_bstride_out = (long long)nt * C->Emax;
   A.smp_ld = C->Emax;
   long long adj_launch = 0;
   for (int j = plan.jL; j >= 0; j--) {
-    if ((rc = run_steps(C, false, F, rc_off[j], rc_n[j], nsamp, B, th, tp, tc, tg, st, &adj_launch)) != FWI_OK)
-      return rc;
-    if ((rc = run_steps(C, true, A, ad_off[j], ad_n[j], nsamp, B, th, tp, tc, tg, st, &adj_launch)) != FWI_OK)
-      return rc;
+    if ((rc = run_steps(C, false, F, rc_off[j], rc_n[j], nsamp, B, M, st, &adj_launch)) != FWI_OK) return rc;
+    if ((rc = run_steps(C, true, A, ad_off[j], ad_n[j], nsamp, B, M, st, &adj_launch)) != FWI_OK) return rc;
   }
   C->launches[2] += adj_launch;
   prof_mark(C, 3, st);
@@ -1096,8 +1153,8 @@ static int gradient_chunk(fwi_ctx* C, const float* vel, int nsamp, const int32_t
                            reinterpret_cast<const int*>(C->dlist + cl.src_cnt),
                            reinterpret_cast<const long long*>(C->dlist + cl.src_pos),
                            reinterpret_cast<const float*>(C->dlist + cl.src_amp), C->stmp, C->G, C->L.field,
-                           g_per_wf, st));
-  CK(launch_finalize(C->L, vel, C->G, nsamp, g_per_wf ? nsg : 1, scale, grad, st));
+                           wf_per_acc, st));
+  CK(launch_finalize(C->L, vel, C->G, nsamp, nsg / wf_per_acc, scale, grad, st));
   C->launches[3] += 3;
   prof_mark(C, 4, st);
   if (C->prof) {  // accumulate this chunk's phase times
@@ -1144,7 +1201,9 @@ static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t
       cost = nchunks * ((2.0 * nt + (double)p.recompute) * std::max(per_cta * 1.7e-6, 15e-6) +
                         (1.0 + 2.0 * (p.jL + 1)) * 20e-6);
     } else {
-      const double waves = std::ceil((double)c * nsg * C->ntiles / nsm);
+      // CTAs of a step launch: tiles x wavefields (x pairs with pair tiles)
+      const int sh = shape_adj(C, nsg);
+      const double waves = std::ceil((double)c * nsg / (sh ? 2 : 1) * C->ntiles_s[sh] / nsm);
       const double t_wave = (double)TX3 * TY3 * C->L.nzp * 16.0 / (6e12 / nsm);
       const double t_launch = std::max(8e-6, waves * t_wave);
       cost = nchunks * (2.0 * nt + (double)p.recompute) * t_launch;

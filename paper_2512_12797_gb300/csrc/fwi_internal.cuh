@@ -82,6 +82,7 @@ struct StepParams {
   int* done;
   int order3;               // 3D CTA order: 0 tile-major, 1 wavefield-fastest
   int zpair3;               // 3D march: 0 one level at a time, 1 two levels together
+  int pair3;                // 3D tiles: 0 one wavefield over 64 x 16, 1 two supergathers over 64 x 8 each
 };
 
 // Host-side launchers (stencil.cu)
@@ -108,7 +109,7 @@ cudaError_t launch_misfit(int nsamp, int nsg, const double* part, int nblk, doub
 cudaError_t launch_source_imaging(int B, int nsg, int nt, int E, const float* qsrc,
                                   const float* wav, const int* src_cnt, const long long* src_pos,
                                   const float* src_amp, float* tmp, float* grad,
-                                  long long field, bool per_wavefield, cudaStream_t st);
+                                  long long field, int wf_per_acc, cudaStream_t st);
 cudaError_t launch_finalize(const Layout& L, const float* vel, const float* G, int nsamp, int g_per_sample,
                             double scale, float* grad, cudaStream_t st);
 cudaError_t launch_langevin(float* z, const float* g, long long n, double eta, double nu,

@@ -23,29 +23,53 @@
 // and lane 0 of warp 8 (a producer warpgroup that setmaxnreg shrinks) refills
 // the ring in sequence order, waiting on each slot's "empty" barrier, so that
 // no consumer warp carries the refill work.
+//
+// Pair tiles (PAIR): a CTA runs two wavefields of one sample (supergathers
+// 2i and 2i+1) over a 64 x 8 column each: warps 0-3 the first, warps 4-7 the
+// second, two rows per warp as above.  The cc plane is loaded once for both,
+// and in the adjoint the two supergathers' imaging terms meet in shared
+// memory (the second wavefield's warp hands its q L p to the first's, through
+// a two-buffer exchange guarded by mbarriers) and go into one accumulator per
+// pair: G += q_a L p_a + q_b L p_b.  The forward's arithmetic per point is
+// the same in both tile forms; the adjoint's accumulator sums in another order
+// than the per-wavefield form, so the library picks the adjoint's form by
+// rule (pairs whenever a sample has an even number of supergathers), not by
+// timing.
 #include "fwi_internal.cuh"
 
 namespace fwi {
 
-constexpr int HY3 = TY3 + 2 * HALO;  // 24
-constexpr int PLANE = HY3 * HX3;     // floats in a halo plane
-constexpr int PPLANE = TY3 * TX3;    // floats in a plain plane
 constexpr int NCW3 = TY3 / 2;        // consumer warps (two y rows each)
 constexpr int NTHREADS3 = 32 * NCW3 + 128;  // + producer warpgroup
 constexpr int REG3_LAUNCH = 168, REG3_PRODUCER = 72, REG3_CONSUMER = 216;
 static_assert(128 * REG3_PRODUCER + 32 * NCW3 * REG3_CONSUMER <= NTHREADS3 * REG3_LAUNCH,
               "register split exceeds the launch allocation");
 
-template <bool ADJ>
+// One ring stage: per wavefield the halo plane of the stepped level (and of
+// the snapshot), per wavefield the plain plane of the older level, then the
+// shared cc plane and (adjoint) the accumulator plane.  Every part starts on
+// a 128-byte boundary.
+template <bool ADJ, bool PAIR>
 struct Smem3D {
-  static constexpr int NST = ADJ ? 8 : 10;  // ring slots
-  static constexpr int OFF_SNAP = PLANE;
-  static constexpr int OFF_PREV = PLANE * (ADJ ? 2 : 1);
-  static constexpr int OFF_CC = OFF_PREV + PPLANE;
+  static constexpr int NWF = PAIR ? 2 : 1;    // wavefields per CTA
+  static constexpr int TYW = TY3 / NWF;       // rows of a wavefield's tile (16 or 8)
+  static constexpr int HYW = TYW + 2 * HALO;
+  static constexpr int PLANE = HYW * HX3;     // floats in one wavefield's halo plane
+  static constexpr int PPLANE = TYW * TX3;    // floats in one wavefield's plain plane
+  static constexpr int NST = ADJ ? 8 : 10;    // ring slots
+  static constexpr int OFF_SNAP = NWF * PLANE;
+  static constexpr int OFF_PREV = NWF * PLANE * (ADJ ? 2 : 1);
+  static constexpr int OFF_CC = OFF_PREV + NWF * PPLANE;
   static constexpr int OFF_G = OFF_CC + PPLANE;
   static constexpr int STAGE = OFF_G + (ADJ ? PPLANE : 0);
-  static constexpr int OFF_GZ = NST * STAGE;  // gamma*dt of every z level
-  static size_t bytes(int nzp) { return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + 2 * NST * 8 + 16; }
+  static constexpr int OFF_X = NST * STAGE;   // pair exchange of the adjoint: 2 buffers of one plane
+  static constexpr int OFF_GZ = OFF_X + (ADJ && PAIR ? 2 * PPLANE : 0);  // gamma*dt of every z level
+  static constexpr int NXB = ADJ && PAIR ? 16 : 0;  // exchange barriers: full[4][2], empty[4][2]
+  static size_t bytes(int nzp) {
+    return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + (2 * NST + NXB) * 8 + 16;
+  }
+  static_assert((PLANE * 4) % 128 == 0 && (PPLANE * 4) % 128 == 0 && (STAGE * 4) % 128 == 0,
+                "stage parts must stay 128-byte aligned");
 };
 
 __device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -122,10 +146,11 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   }
 }
 
-template <bool ADJ, bool ISO, int NQ>
+template <bool ADJ, bool ISO, int NQ, bool PAIR>
 struct March3D {
-  using S = Smem3D<ADJ>;
+  using S = Smem3D<ADJ, PAIR>;
   static constexpr int NST = S::NST;
+  static constexpr int PLANE = S::PLANE, PPLANE = S::PPLANE;
   const Layout& L;
   const Coef& K;
   const StepParams& P;
@@ -136,8 +161,13 @@ struct March3D {
   float* sm;
   uint64_t* full;
   uint64_t* empty;
+  uint64_t* xfull;       // pair exchange (adjoint): [pair of warps][buffer]
+  uint64_t* xempty;
   volatile int* abort_flag;
   int lane, ly, lx, x0, y0, gx, gy, b, s, tile, last_q;
+  int b0, k;             // first wavefield of the CTA, this warp's wavefield index in it
+  int xpair;             // pair tiles: index of this warp within its wavefield's group (0-3)
+  int acc;               // imaging accumulator of this warp's wavefield (per wavefield or per pair)
   bool colv;
   float gyv, gxv[4];
   const float* gz;       // shared gamma*dt per z level
@@ -154,14 +184,21 @@ struct March3D {
     const int zh = pq - HALO, zp = pq - 2 * HALO;
     const bool plain = zp >= 0 && zp < L.nzp;
     float* base = sm + pst * S::STAGE;
-    uint32_t bytes = PLANE * 4 * (ADJ ? 2 : 1) + (plain ? PPLANE * 4 * (ADJ ? 3 : 2) : 0);
+    const uint32_t bytes = S::NWF * PLANE * 4 * (ADJ ? 2 : 1) +
+                           (plain ? (S::NWF * PPLANE + PPLANE * (ADJ ? 2 : 1)) * 4 : 0);
     mbar_arrive_expect_tx(&full[pst], bytes);
-    tma_load_5d(base, th, x0, y0, zh + HALO, b, P.s_cur, &full[pst]);
-    if (ADJ) tma_load_5d(base + S::OFF_SNAP, th, x0, y0, zh + HALO, b, P.s_snap, &full[pst]);
+#pragma unroll
+    for (int w = 0; w < S::NWF; w++) {
+      tma_load_5d(base + w * PLANE, th, x0, y0, zh + HALO, b0 + w, P.s_cur, &full[pst]);
+      if (ADJ) tma_load_5d(base + S::OFF_SNAP + w * PLANE, th, x0, y0, zh + HALO, b0 + w, P.s_snap, &full[pst]);
+    }
     if (plain) {
-      tma_load_5d(base + S::OFF_PREV, tp, x0 + HALO, y0 + HALO, zp + HALO, b, P.s_prev, &full[pst]);
+#pragma unroll
+      for (int w = 0; w < S::NWF; w++)
+        tma_load_5d(base + S::OFF_PREV + w * PPLANE, tp, x0 + HALO, y0 + HALO, zp + HALO, b0 + w, P.s_prev,
+                    &full[pst]);
       tma_load_4d(base + S::OFF_CC, tcc, x0 + HALO, y0 + HALO, zp + HALO, s, &full[pst]);
-      if (ADJ) tma_load_4d(base + S::OFF_G, tg, x0 + HALO, y0 + HALO, zp + HALO, b, &full[pst]);
+      if (ADJ) tma_load_4d(base + S::OFF_G, tg, x0 + HALO, y0 + HALO, zp + HALO, PAIR ? b0 / 2 : b0, &full[pst]);
     }
     pq++;
     if (++pst == NST) { pst = 0; pround ^= 1; }
@@ -173,7 +210,7 @@ struct March3D {
   template <int CI>
   __device__ __forceinline__ bool land() {
     if (!mbar_wait_abortable(&full[cslot], cphase, P.status, abort_flag)) return false;
-    const float* stage = sm + cslot * S::STAGE;
+    const float* stage = sm + cslot * S::STAGE + k * PLANE;
     Q[CI] = ld4s(stage + (ly + HALO) * HX3 + lx + HALO);
     if (ADJ) QS[CI] = ld4s(stage + S::OFF_SNAP + (ly + HALO) * HX3 + lx + HALO);
     if (++cslot == NST) {
@@ -187,14 +224,14 @@ struct March3D {
   // plane), queue centre at compile-time index C = (q - 4) % NQ; then the
   // slot of sequence q - 4 is released.
   template <int C>
-  __device__ __forceinline__ void level(int q) {
+  __device__ __forceinline__ bool level(int q) {
     float* stage = sm + lslot * S::STAGE;
     const int z = q - 2 * HALO;
     if (z >= 0) {
-      const float* hpl = sm + hslot * S::STAGE;  // halo plane of level z (sequence q - 4)
+      const float* hpl = sm + hslot * S::STAGE + k * PLANE;  // halo plane of level z (sequence q - 4)
       float lap[4];
       lap3<C, ISO, NQ>(hpl, Q, ly, lx, K, lap);
-      const float4 pm = ld4s(stage + S::OFF_PREV + ly * TX3 + lx);
+      const float4 pm = ld4s(stage + S::OFF_PREV + k * PPLANE + ly * TX3 + lx);
       const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
       const float gzy = gz[z] + gyv;
       float nv[4];
@@ -211,7 +248,7 @@ struct March3D {
       // the p^{n-1} plane (already consumed); entry .x is the point's index
       // in that plane, and its row / 2 names the warp that owns it
       if (inj_z == z || smp_z == z) {
-        float* pl = stage + S::OFF_PREV;
+        float* pl = stage + S::OFF_PREV + k * PPLANE;
         const int wrow = ly >> 1;
         __syncwarp();
         *reinterpret_cast<float4*>(pl + ly * TX3 + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
@@ -244,15 +281,43 @@ struct March3D {
       if (ADJ) {
         float lps[4];
         lap3<C, ISO, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
-        const float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
-        if (colv) {
-          float* gp = P.grad + (long long)b * L.field + L.off(z, gy, gx);
+        float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
+        if (PAIR) {
+          // the second wavefield's warp hands q L p to the first's (buffer z & 1,
+          // use z >> 1); the first adds both to the pair's accumulator
+          const int xb = z & 1, use = z >> 1, pr = xpair;
+          float* xp = sm + S::OFF_X + xb * PPLANE + ly * TX3 + lx;
+          if (k == 1) {
+            if (use > 0 && !mbar_wait_abortable(&xempty[pr * 2 + xb], (uint32_t)((use - 1) & 1), P.status,
+                                                 abort_flag))
+              return false;
+            const float2 c01 = __fmul2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]));
+            const float2 c23 = __fmul2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]));
+            *reinterpret_cast<float4*>(xp) = make_float4(c01.x, c01.y, c23.x, c23.y);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xfull[pr * 2 + xb]);
+          } else {
+            if (!mbar_wait_abortable(&xfull[pr * 2 + xb], (uint32_t)(use & 1), P.status, abort_flag)) return false;
+            const float4 cb = ld4s(xp);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xempty[pr * 2 + xb]);
+            const float2 g01 = __fadd2_rn(__ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y)),
+                                          f2(cb.x, cb.y));
+            const float2 g23 = __fadd2_rn(__ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w)),
+                                          f2(cb.z, cb.w));
+            g = make_float4(g01.x, g01.y, g23.x, g23.y);
+          }
+        } else {
           const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
           const float2 g23 = __ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w));
-          const float gv[4] = {g01.x, g01.y, g23.x, g23.y};
+          g = make_float4(g01.x, g01.y, g23.x, g23.y);
+        }
+        if (colv && (!PAIR || k == 0)) {
+          float* gp = P.grad + (long long)acc * L.field + L.off(z, gy, gx);
           if (gx + 3 < L.nxp) {
-            *reinterpret_cast<float4*>(gp) = make_float4(gv[0], gv[1], gv[2], gv[3]);
+            *reinterpret_cast<float4*>(gp) = g;
           } else {
+            const float gv[4] = {g.x, g.y, g.z, g.w};
             for (int j = 0; j < 4; j++)
               if (gx + j < L.nxp) gp[j] = gv[j];
           }
@@ -275,40 +340,52 @@ struct March3D {
     }
     if (++lslot == NST) lslot = 0;
     if (++hslot == NST) hslot = 0;
+    return true;
   }
 };
 
-template <bool ADJ, bool ISO, int NQ>
+template <bool ADJ, bool ISO, int NQ, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS3, 1)
 step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_cc, const __grid_constant__ CUtensorMap tm_g, const Layout L,
               const Coef K, const StepParams P) {
-  using S = Smem3D<ADJ>;
+  using S = Smem3D<ADJ, PAIR>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* gz = sm + S::OFF_GZ;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (((size_t)S::OFF_GZ + ((L.nzp + 31) / 32) * 32) * 4));
   uint64_t* empty = full + S::NST;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST);
+  uint64_t* xfull = empty + S::NST;
+  uint64_t* xempty = xfull + S::NXB / 2;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST + S::NXB);
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  March3D<ADJ, ISO, NQ> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, abort_flag};
+  March3D<ADJ, ISO, NQ, PAIR> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, xfull, xempty,
+                                abort_flag};
   M.lane = tid & 31;
-  M.ly = 2 * warp + (tid >> 4 & 1);
-  // CTA -> (wavefield, tile): tile-major order runs all tiles of a wavefield
-  // back to back; wavefield-fastest order runs the tile of every wavefield
-  // of the launch side by side, so the supergathers of a sample read the
-  // same cc plane within microseconds of each other (one DRAM read, the
-  // others L2 hits)
+  // warp -> (wavefield of the CTA, rows): one wavefield over 16 rows, or
+  // (pair tiles) warps 0-3 and 4-7 over 8 rows of the first and second
+  constexpr int WPG = NCW3 / S::NWF;  // consumer warps per wavefield
+  M.k = warp < NCW3 ? warp / WPG : 0;
+  M.xpair = warp % WPG;
+  M.ly = 2 * (warp % WPG) + (tid >> 4 & 1);
+  // CTA -> (wavefield unit, tile): tile-major order runs all tiles of a unit
+  // back to back; wavefield-fastest order runs the tile of every unit of the
+  // launch side by side, so the supergathers of a sample read the same cc
+  // plane within microseconds of each other (one DRAM read, the others L2
+  // hits).  A unit is one wavefield, or two (pair tiles).
   {
-    const int nb = gridDim.x / P.ntiles;
+    const int nu = gridDim.x / P.ntiles;
     const int idx = blockIdx.x;
-    M.b = P.order3 ? idx % nb : idx / P.ntiles;
-    M.tile = P.order3 ? idx / nb : idx % P.ntiles;
+    const int u = P.order3 ? idx % nu : idx / P.ntiles;
+    M.tile = P.order3 ? idx / nu : idx % P.ntiles;
+    M.b0 = u * S::NWF;
   }
+  M.b = M.b0 + M.k;
+  M.acc = PAIR ? M.b0 / 2 : M.b;
   M.x0 = (M.tile % P.ntx) * TX3;
-  M.y0 = (M.tile / P.ntx) * TY3;
-  M.s = M.b / P.nsg;
+  M.y0 = (M.tile / P.ntx) * S::TYW;
+  M.s = M.b0 / P.nsg;
   M.lx = 4 * (M.lane & 15);
   M.gx = M.x0 + M.lx;
   M.gy = M.y0 + M.ly;
@@ -320,7 +397,7 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.pround = 0;
   M.cslot = 0;
   M.lslot = 0;
-  M.hslot = Smem3D<ADJ>::NST - HALO;  // (0 - 4) mod NST: first used at q = 4
+  M.hslot = S::NST - HALO;  // (0 - 4) mod NST: first used at q = 4
   M.cphase = 0;
 
   if (tid == 0) {
@@ -332,6 +409,7 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], NCW3);
     }
+    for (int i = 0; i < S::NXB; i++) mbar_init(&xfull[i], 1);  // xfull and xempty: one arrival each
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -380,14 +458,14 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   // level at a time.  NQ = 10: two sequences land, then their two levels are
   // computed together (two independent chains per thread), the queue holding
   // levels z - 4 .. z + 5.
-#define FWI_ONE(k)                                  \
-  if (!M.template land<(k) % NQ>()) return;         \
-  M.template level<((k) + NQ - 4) % NQ>(q + (k));
-#define FWI_TWO(k)                                  \
-  if (!M.template land<(k)>()) return;              \
-  if (!M.template land<(k) + 1>()) return;          \
-  M.template level<((k) + 6) % 10>(q + (k));        \
-  M.template level<((k) + 7) % 10>(q + (k) + 1);
+#define FWI_ONE(k)                                          \
+  if (!M.template land<(k) % NQ>()) return;                 \
+  if (!M.template level<((k) + NQ - 4) % NQ>(q + (k))) return;
+#define FWI_TWO(k)                                          \
+  if (!M.template land<(k)>()) return;                      \
+  if (!M.template land<(k) + 1>()) return;                  \
+  if (!M.template level<((k) + 6) % 10>(q + (k))) return;   \
+  if (!M.template level<((k) + 7) % 10>(q + (k) + 1)) return;
   int q = 0;
   if constexpr (NQ == 9) {
     for (; q + 9 <= M.last_q + 1; q += 9) {
@@ -417,12 +495,12 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
 #undef FWI_TWO
 }
 
-template <bool ADJ, bool ISO>
+template <bool ADJ, bool ISO, bool PAIR>
 static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
                            const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, dim3 grid,
                            cudaStream_t st) {
-  const size_t bytes = Smem3D<ADJ>::bytes(L.nzp);
-  auto kern = P.zpair3 ? step3d_kernel<ADJ, ISO, 10> : step3d_kernel<ADJ, ISO, 9>;
+  const size_t bytes = Smem3D<ADJ, PAIR>::bytes(L.nzp);
+  auto kern = P.zpair3 ? step3d_kernel<ADJ, ISO, 10, PAIR> : step3d_kernel<ADJ, ISO, 9, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   kern<<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
@@ -432,15 +510,22 @@ static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_pla
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
                           const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, int B,
                           cudaStream_t st) {
-  dim3 grid((unsigned)(P.ntiles * B));
+  // grid: tiles x units (one wavefield, or a pair of supergathers of one sample)
+  if (P.pair3 && (B % 2 || P.nsg % 2)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(P.ntiles * (P.pair3 ? B / 2 : B)));
   // The one-bracket form serves the forward only: on the layered 3D batch
   // it made the forward step 4 % faster and the adjoint step (two
   // Laplacians) 2 % slower.
-  if (adj) return launch3<true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+  if (adj)
+    return P.pair3 ? launch3<true, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
+                   : launch3<true, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
   bool iso = true;
   for (int k = 1; k <= 4; k++) iso = iso && K.cx[k] == K.cy[k] && K.cx[k] == K.cz[k];
-  return iso ? launch3<false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
-             : launch3<false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+  if (P.pair3)
+    return iso ? launch3<false, true, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
+               : launch3<false, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+  return iso ? launch3<false, true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
+             : launch3<false, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
 }
 
 }  // namespace fwi

@@ -68,11 +68,14 @@ def test_forward_3d_medium_matches_oracle(P):
     assert e < FWD_TOL, e
 
 
-def test_gradient_3d_batched_matches_oracle(P):
+@pytest.mark.parametrize("sg", [[3, 1], [2, 1, 1]])
+def test_gradient_3d_batched_matches_oracle(P, sg):
+    # two supergathers per sample: the adjoint runs on pair tiles (one imaging
+    # accumulator per pair); three: on one-wavefield tiles
     import torch
     w = medium3d(nt=150)
     g = O.Grid.from_workload(w)
-    nsamp, sg = 2, [3, 1]
+    nsamp = 2
     vs = np.stack([synth.models.random_smooth_model(w.shape, 30 + s, 1500, 3000) for s in range(nsamp)])
     d_obs = synth.random_records(w, 8)
     encs = [P.encode(2, s, w.ns) for s in range(nsamp)]
@@ -153,9 +156,10 @@ def test_chunked_gradient_3d_bit_identical(P):
 
 def test_3d_step_variants_bit_identical(P):
     # the autotuner's 3D variants (CTA order; one or two z levels per march
-    # step) change only which CTA runs which tile when and how a thread's
-    # instructions interleave, not any point's arithmetic, so forced choices
-    # give bit-identical gradients
+    # step; for the forward, 64 x 16 tiles or 64 x 8 pair tiles) change only
+    # which CTA runs which tile when and how a thread's instructions
+    # interleave, not any point's arithmetic, so forced choices give
+    # bit-identical records and gradients
     import torch
     w = medium3d(nt=60)
     v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 70 + s, 1500, 3000)
@@ -165,13 +169,18 @@ def test_3d_step_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    for var in ((0, 0), (1, 1), (2, 3), (3, 2)):
+    for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3)):
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
-        out.append(ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0))
+        m, g = ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
+        rec = ctx.forward(v, perm, wt, [2, 2])
+        out.append((m, g, rec))
         got = ctx.variants()
         assert (got["forward"], got["adjoint"]) == var
+        if var[0] >= 4:
+            assert "pairs" in got["forward_name"]
+        assert "pairs" in got["adjoint_name"]  # two supergathers per sample
         ctx.close()
     torch.cuda.synchronize()
-    for m, g in out[1:]:
-        assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0])
+    for m, g, rec in out[1:]:
+        assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0]) and torch.equal(rec, out[0][2])
