@@ -510,11 +510,15 @@ int validate_call(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, 
 }
 
 // 3D tile shape of the forward kernel (the autotuned variant's bit 2) and of
-// the adjoint kernel (by rule: pair tiles whenever a sample has an even
-// number of supergathers, since the pair form sums the imaging term in
-// another order); 2D has one shape.
+// the adjoint kernel: 64 x 16 tiles unless a forced variant sets bit 2 (pair
+// tiles, for a sample with an even number of supergathers).  The autotuner
+// does not choose the adjoint's shape, since the pair form sums the imaging
+// term in another order and a timing-dependent choice would make results
+// depend on the run; 2D has one shape.
 int shape_fwd(const fwi_ctx* C) { return C->L.ndim == 3 ? (C->var[0] >> 2) & 1 : 0; }
-int shape_adj(const fwi_ctx* C, int nsg) { return C->L.ndim == 3 && nsg % 2 == 0 ? 1 : 0; }
+int shape_adj(const fwi_ctx* C, int nsg) {
+  return C->L.ndim == 3 && nsg % 2 == 0 && C->var[1] >= 0 && (C->var[1] & 4) ? 1 : 0;
+}
 
 StepParams base_params(fwi_ctx* C, int B, int nsg, int sh = 0) {
   StepParams P;
@@ -594,7 +598,7 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
 // step, and for the forward bit 2 the tile shape (64 x 16, or 64 x 8 pair
 // tiles, offered when a sample has an even number of supergathers).  The 3D
 // adjoint's tile shape follows shape_adj.
-int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? (adj ? 4 : 8) : num_variants2d(adj); }
+int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 8 : num_variants2d(adj); }
 const char* variant_name(const fwi_ctx* C, bool adj, int v) {
   if (C->L.ndim == 2) return variant2d_name(adj, v);
   static const char* fwd[8] = {
@@ -608,7 +612,7 @@ const char* variant_name(const fwi_ctx* C, bool adj, int v) {
       {"adj3d 64x8 pairs tile-major, 1 level", "adj3d 64x8 pairs wavefield-fastest, 1 level",
        "adj3d 64x8 pairs tile-major, 2 levels", "adj3d 64x8 pairs wavefield-fastest, 2 levels"}};
   if (v < 0) return "-";
-  return adj ? (v < 4 ? adjn[C->adj_pair][v] : "-") : (v < 8 ? fwd[v] : "-");
+  return adj ? (v < 8 ? adjn[C->adj_pair][v & 3] : "-") : (v < 8 ? fwd[v] : "-");
 }
 
 // kTuneSteps steps of variant v: one multi-step launch in 2D, one launch per
@@ -642,8 +646,12 @@ cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDes
 // accumulators, which every gradient chunk clears after tuning.
 int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cudaStream_t st) {
   const int B = nsamp * nsg;
+  if (C->tuned_B == B && C->tuned_nsg == nsg && C->var[0] >= 0 && C->var[1] >= 0) {
+    C->adj_pair = shape_adj(C, nsg);
+    return FWI_OK;
+  }
+  C->var[1] = C->forced[1] >= 0 ? C->forced[1] : -1;
   C->adj_pair = shape_adj(C, nsg);
-  if (C->tuned_B == B && C->tuned_nsg == nsg && C->var[0] >= 0 && C->var[1] >= 0) return FWI_OK;
   // timing steps with the traffic of real ones: the three ring slots rotate
   // (whatever they hold), the snapshot comes from a fourth slot when there is one
   StepDesc td[kTuneSteps];
@@ -667,6 +675,7 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cu
     int best = -1;
     float best_ms = 1e30f;
     for (int v = 0; v < nv && v < 8; v++) {
+      if (C->L.ndim == 3 && adj && v >= 4) break;  // the adjoint's tile shape follows the rule
       // pair tiles need an even number of supergathers per sample
       const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : 0;
       if (sh && nsg % 2) continue;

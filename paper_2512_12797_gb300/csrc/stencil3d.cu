@@ -179,6 +179,34 @@ struct March3D {
   int ie_cur, ie_end, se_cur, se_end;  // point-list cursors (entries sorted by z)
   int inj_z, smp_z;                    // z of the entries under the cursors (INT_MAX: none left)
   float4 Q[NQ], QS[NQ];
+  float4 gpend;          // pair tiles, first wavefield's warps: G + q_a L p_a of the previous level
+
+  // Imaging accumulator row of level z (this thread's 4 points).
+  __device__ __forceinline__ void store_g(int z, const float4& g) {
+    if (!colv) return;
+    float* gp = P.grad + (long long)acc * L.field + L.off(z, gy, gx);
+    if (gx + 3 < L.nxp) {
+      *reinterpret_cast<float4*>(gp) = g;
+    } else {
+      const float gv[4] = {g.x, g.y, g.z, g.w};
+      for (int j = 0; j < 4; j++)
+        if (gx + j < L.nxp) gp[j] = gv[j];
+    }
+  }
+
+  // Pair tiles, first wavefield's warps: adds the second wavefield's q L p of
+  // level zp (buffer zp & 1) to gpend and stores the pair's accumulator.
+  __device__ __forceinline__ bool pair_finish(int zp) {
+    const int xb = zp & 1, use = zp >> 1, pr = xpair;
+    if (!mbar_wait_abortable(&xfull[pr * 2 + xb], (uint32_t)(use & 1), P.status, abort_flag)) return false;
+    const float4 cb = ld4s(sm + S::OFF_X + xb * PPLANE + ly * TX3 + lx);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&xempty[pr * 2 + xb]);
+    const float2 g01 = __fadd2_rn(f2(gpend.x, gpend.y), f2(cb.x, cb.y));
+    const float2 g23 = __fadd2_rn(f2(gpend.z, gpend.w), f2(cb.z, cb.w));
+    store_g(zp, make_float4(g01.x, g01.y, g23.x, g23.y));
+    return true;
+  }
 
   __device__ __forceinline__ void issue() {
     const int zh = pq - HALO, zp = pq - 2 * HALO;
@@ -283,44 +311,33 @@ struct March3D {
         lap3<C, ISO, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
         float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (PAIR) {
-          // the second wavefield's warp hands q L p to the first's (buffer z & 1,
-          // use z >> 1); the first adds both to the pair's accumulator
-          const int xb = z & 1, use = z >> 1, pr = xpair;
-          float* xp = sm + S::OFF_X + xb * PPLANE + ly * TX3 + lx;
+          // The second wavefield's warp hands q L p of level z to the first's
+          // through buffer z & 1; the first takes it one level later (level
+          // z + 1, or the flush after the last level), so that neither warp
+          // waits for the other's current level: it keeps G + q_a L p_a of
+          // level z in registers until then.
+          const int pr = xpair;
           if (k == 1) {
+            const int xb = z & 1, use = z >> 1;
             if (use > 0 && !mbar_wait_abortable(&xempty[pr * 2 + xb], (uint32_t)((use - 1) & 1), P.status,
                                                  abort_flag))
               return false;
             const float2 c01 = __fmul2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]));
             const float2 c23 = __fmul2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]));
-            *reinterpret_cast<float4*>(xp) = make_float4(c01.x, c01.y, c23.x, c23.y);
+            *reinterpret_cast<float4*>(sm + S::OFF_X + xb * PPLANE + ly * TX3 + lx) =
+                make_float4(c01.x, c01.y, c23.x, c23.y);
             __syncwarp();
             if (lane == 0) mbar_arrive(&xfull[pr * 2 + xb]);
           } else {
-            if (!mbar_wait_abortable(&xfull[pr * 2 + xb], (uint32_t)(use & 1), P.status, abort_flag)) return false;
-            const float4 cb = ld4s(xp);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&xempty[pr * 2 + xb]);
-            const float2 g01 = __fadd2_rn(__ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y)),
-                                          f2(cb.x, cb.y));
-            const float2 g23 = __fadd2_rn(__ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w)),
-                                          f2(cb.z, cb.w));
-            g = make_float4(g01.x, g01.y, g23.x, g23.y);
+            if (z > 0 && !pair_finish(z - 1)) return false;
+            const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
+            const float2 g23 = __ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w));
+            gpend = make_float4(g01.x, g01.y, g23.x, g23.y);
           }
         } else {
           const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
           const float2 g23 = __ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w));
-          g = make_float4(g01.x, g01.y, g23.x, g23.y);
-        }
-        if (colv && (!PAIR || k == 0)) {
-          float* gp = P.grad + (long long)acc * L.field + L.off(z, gy, gx);
-          if (gx + 3 < L.nxp) {
-            *reinterpret_cast<float4*>(gp) = g;
-          } else {
-            const float gv[4] = {g.x, g.y, g.z, g.w};
-            for (int j = 0; j < 4; j++)
-              if (gx + j < L.nxp) gp[j] = gv[j];
-          }
+          store_g(z, make_float4(g01.x, g01.y, g23.x, g23.y));
         }
       }
       if (colv) {
@@ -493,6 +510,8 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   }
 #undef FWI_ONE
 #undef FWI_TWO
+  // pair tiles: the first wavefield's warps still hold the last level
+  if (ADJ && PAIR && M.k == 0 && L.nzp > 0) M.pair_finish(L.nzp - 1);
 }
 
 template <bool ADJ, bool ISO, bool PAIR>

@@ -68,10 +68,10 @@ def test_forward_3d_medium_matches_oracle(P):
     assert e < FWD_TOL, e
 
 
-@pytest.mark.parametrize("sg", [[3, 1], [2, 1, 1]])
-def test_gradient_3d_batched_matches_oracle(P, sg):
-    # two supergathers per sample: the adjoint runs on pair tiles (one imaging
-    # accumulator per pair); three: on one-wavefield tiles
+@pytest.mark.parametrize("sg,adj_variant", [([3, 1], -1), ([3, 1], 4), ([2, 1, 1], -1)])
+def test_gradient_3d_batched_matches_oracle(P, sg, adj_variant):
+    # adj_variant 4: the adjoint on pair tiles (two supergathers per CTA, one
+    # imaging accumulator per pair); -1: autotuned, one-wavefield tiles
     import torch
     w = medium3d(nt=150)
     g = O.Grid.from_workload(w)
@@ -82,7 +82,9 @@ def test_gradient_3d_batched_matches_oracle(P, sg):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     ctx = P.FWI(w.grid_dict(), w.src, w.rec, nsamp * len(sg), 1 << 31)
+    ctx.set_variants(-1, adj_variant)
     mis, grad = ctx.gradient(torch.tensor(vs).cuda(), perm, wt, sg, torch.tensor(d_obs).cuda(), 0.3)
+    assert ("pairs" in ctx.variants()["adjoint_name"]) == (adj_variant >= 4)
     torch.cuda.synchronize()
     assert ctx.device_status() == 0
     for s in range(nsamp):
@@ -169,7 +171,7 @@ def test_3d_step_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3)):
+    for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3)):  # adjoint on 64 x 16 tiles
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
         m, g = ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
@@ -179,8 +181,34 @@ def test_3d_step_variants_bit_identical(P):
         assert (got["forward"], got["adjoint"]) == var
         if var[0] >= 4:
             assert "pairs" in got["forward_name"]
-        assert "pairs" in got["adjoint_name"]  # two supergathers per sample
         ctx.close()
     torch.cuda.synchronize()
     for m, g, rec in out[1:]:
         assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0]) and torch.equal(rec, out[0][2])
+
+
+def test_3d_pair_tile_adjoint_variants_bit_identical(P):
+    # the pair-tile adjoint's CTA orders and march forms agree bit for bit,
+    # and with the 64 x 16 adjoint to FP32 rounding (another summation order
+    # of the imaging term)
+    import torch
+    w = medium3d(nt=60)
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 80 + s, 1500, 3000)
+                               for s in range(2)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 12)).cuda()
+    encs = [P.encode(9, s, w.ns) for s in range(2)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    out = []
+    for var in ((3, 4), (0, 5), (1, 6), (2, 7), (3, 0)):
+        ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
+        ctx.set_variants(*var)
+        out.append(ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0))
+        assert ("pairs" in ctx.variants()["adjoint_name"]) == (var[1] >= 4)
+        ctx.close()
+    torch.cuda.synchronize()
+    for m, g in out[1:4]:
+        assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0])
+    m0, g0 = out[4]
+    assert torch.equal(m0, out[0][0])
+    assert float((g0 - out[0][1]).norm() / g0.norm()) < 1e-6
