@@ -312,17 +312,26 @@ int fwi_checkpoint_schedule(int nt, int64_t slots, int32_t* desc_out, int cap, i
  * minimises (chunks) x (2 nt + recomputed steps) x (time of one step launch). */
 int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
 
-/* Step-kernel variants: in 2D the TMA ring depth, in 3D the CTA order
- * (0: all tiles of one wavefield back to back, 1: the tile of every wavefield
- * of the launch side by side, so that a sample's supergathers share its cc
- * reads through L2).  By default the first fwi_forward / fwi_gradient call
- * for a given nsamp*nsg times every variant on that shape (synchronising the
- * stream while it does) and keeps the fastest; all variants give
- * bit-identical results.  fwi_set_kernel_variants forces a variant index (-1
- * restores autotuning; FWI_ERR_ARG beyond the variant count);
- * fwi_kernel_variants reports the chosen indices and names and, in
- * ms[0..7], the per-step time of each variant measured by the tuner (-1: not
- * run). */
+/* Step-kernel variants.  2D: the TMA ring depth.  3D: variant bits
+ *   bit 0  CTA order: all tiles of one wavefield back to back, or the tile of
+ *          every wavefield of the launch side by side (a sample's supergathers
+ *          then share its cc reads through L2);
+ *   bit 1  one z level per march step, or two computed together;
+ *   bit 2  tile shape: 64 x 16 columns of one wavefield, or 64 x 8 columns of
+ *          two supergathers of one sample per CTA (cc shared; in the adjoint
+ *          one imaging accumulator per pair), when a sample has an even
+ *          number of supergathers;
+ *   bit 3  one CTA per column, or a persistent grid of one CTA per SM that
+ *          runs its columns back to back.
+ * By default the first fwi_forward / fwi_gradient call for a given
+ * (nsamp*nsg, nsg) times every variant on that shape (synchronising the stream
+ * while it does) and keeps the fastest; the variants it chooses among give
+ * bit-identical results.  The 3D adjoint's tile shape (bit 2) is not tuned:
+ * the pair form sums the imaging term in another order, so it is used only
+ * when forced.  fwi_set_kernel_variants forces a variant index (-1 restores
+ * autotuning; FWI_ERR_ARG beyond the variant count); fwi_kernel_variants
+ * reports the chosen indices and names and, in ms[0..15], the per-step time
+ * of each variant measured by the tuner (-1: not run). */
 int fwi_set_kernel_variants(fwi_ctx* ctx, int fwd, int adj);
 int fwi_kernel_variants(fwi_ctx* ctx, int* fwd, int* adj, const char** fwd_name, const char** adj_name,
                         float* fwd_ms, float* adj_ms, int* nvariants);

@@ -1,6 +1,7 @@
 // fwi_api.cu -- host side of libfwi: context, checkpoint planner, point lists,
 // TMA descriptors and the C ABI entry points declared in fwi.h.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -198,7 +199,7 @@ struct fwi_ctx {
   int forced[2] = {-1, -1};
   int tuned_B = -1, tuned_nsg = -1;  // call shape the variants were tuned for
   int adj_pair = 0;  // tile shape of the 3D adjoint in the last tuned call (shape_adj)
-  float tune_ms[2][8] = {};
+  float tune_ms[2][16] = {};
   int* zero_off = nullptr;  // [ntiles+1] zeros: "no points in any tile"
   float* gtab = nullptr;    // gamma*dt per axis: z [nzp], y [nyp], x [nxp]
   // step descriptors of the current call, in launch order (device, pinned
@@ -555,6 +556,7 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
       P.t = d.t;
       P.order3 = C->var[adj ? 1 : 0] & 1;
       P.zpair3 = (C->var[adj ? 1 : 0] >> 1) & 1;
+      P.ctas_per_sm3 = (C->var[adj ? 1 : 0] >> 3) & 1;
       CK(launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st));
     }
     *launches += n;
@@ -595,24 +597,26 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
 
 // Step-kernel variants: 2D ring depths (stencil.cu).  3D variant v: bit 0
 // the CTA order (tile-major, wavefield-fastest), bit 1 two z levels per march
-// step, and for the forward bit 2 the tile shape (64 x 16, or 64 x 8 pair
-// tiles, offered when a sample has an even number of supergathers).  The 3D
-// adjoint's tile shape follows shape_adj.
-int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 8 : num_variants2d(adj); }
+// step, bit 2 the tile shape (64 x 16, or 64 x 8 pair tiles when a sample
+// has an even number of supergathers; for the adjoint only when forced, see
+// shape_adj), bit 3 a persistent grid of one CTA per SM running its columns
+// back to back (else one CTA per column).
+int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 16 : num_variants2d(adj); }
 const char* variant_name(const fwi_ctx* C, bool adj, int v) {
   if (C->L.ndim == 2) return variant2d_name(adj, v);
-  static const char* fwd[8] = {
-      "fwd3d 64x16 tile-major, 1 level", "fwd3d 64x16 wavefield-fastest, 1 level",
-      "fwd3d 64x16 tile-major, 2 levels", "fwd3d 64x16 wavefield-fastest, 2 levels",
-      "fwd3d 64x8 pairs tile-major, 1 level", "fwd3d 64x8 pairs wavefield-fastest, 1 level",
-      "fwd3d 64x8 pairs tile-major, 2 levels", "fwd3d 64x8 pairs wavefield-fastest, 2 levels"};
-  static const char* adjn[2][4] = {
-      {"adj3d 64x16 tile-major, 1 level", "adj3d 64x16 wavefield-fastest, 1 level",
-       "adj3d 64x16 tile-major, 2 levels", "adj3d 64x16 wavefield-fastest, 2 levels"},
-      {"adj3d 64x8 pairs tile-major, 1 level", "adj3d 64x8 pairs wavefield-fastest, 1 level",
-       "adj3d 64x8 pairs tile-major, 2 levels", "adj3d 64x8 pairs wavefield-fastest, 2 levels"}};
-  if (v < 0) return "-";
-  return adj ? (v < 8 ? adjn[C->adj_pair][v & 3] : "-") : (v < 8 ? fwd[v] : "-");
+  static char names[2][16][64];
+  static bool init = false;
+  if (!init) {
+    for (int a = 0; a < 2; a++)
+      for (int i = 0; i < 16; i++)
+        snprintf(names[a][i], sizeof(names[a][i]), "%s %s %s, %d level%s%s", a ? "adj3d" : "fwd3d",
+                 (i & 4) ? "64x8 pairs" : "64x16", (i & 1) ? "wavefield-fastest" : "tile-major", (i & 2) ? 2 : 1,
+                 (i & 2) ? "s" : "", (i & 8) ? ", persistent" : "");
+    init = true;
+  }
+  if (v < 0 || v > 15) return "-";
+  if (adj && C->adj_pair != ((v >> 2) & 1)) return names[1][v ^ 4];  // the shape the adjoint ran on
+  return names[adj ? 1 : 0][v];
 }
 
 // kTuneSteps steps of variant v: one multi-step launch in 2D, one launch per
@@ -622,6 +626,7 @@ cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDes
   if (C->L.ndim == 3) {
     P.order3 = v & 1;
     P.zpair3 = (v >> 1) & 1;
+    P.ctas_per_sm3 = (v >> 3) & 1;
     const int sh = P.pair3;
     for (int i = 0; i < kTuneSteps; i++) {
       P.s_cur = td[i].cur;
@@ -665,17 +670,17 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cu
   CK(cudaEventCreate(&e1));
   for (int adj = 0; adj < 2; adj++) {
     const int nv = num_variants(C, adj != 0);
-    for (int v = 0; v < 8; v++) C->tune_ms[adj][v] = -1.f;
+    for (int v = 0; v < 16; v++) C->tune_ms[adj][v] = -1.f;
     if (C->forced[adj] >= 0 && C->forced[adj] < nv) {
       // a forced 3D pair-tile forward needs an even number of supergathers:
       // otherwise the same variant with 64 x 16 tiles
-      C->var[adj] = (C->L.ndim == 3 && !adj && nsg % 2) ? (C->forced[adj] & 3) : C->forced[adj];
+      C->var[adj] = (C->L.ndim == 3 && !adj && nsg % 2) ? (C->forced[adj] & ~4) : C->forced[adj];
       continue;
     }
     int best = -1;
     float best_ms = 1e30f;
-    for (int v = 0; v < nv && v < 8; v++) {
-      if (C->L.ndim == 3 && adj && v >= 4) break;  // the adjoint's tile shape follows the rule
+    for (int v = 0; v < nv && v < 16; v++) {
+      if (C->L.ndim == 3 && adj && (v & 4)) continue;  // the adjoint's tile shape is not tuned (shape_adj)
       // pair tiles need an even number of supergathers per sample
       const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : 0;
       if (sh && nsg % 2) continue;
@@ -1387,7 +1392,7 @@ int fwi_kernel_variants(fwi_ctx* C, int* fwd, int* adj, const char** fwd_name, c
   if (adj_name) *adj_name = variant_name(C, true, C->var[1]);
   const int n = std::max(num_variants(C, false), num_variants(C, true));
   if (nvariants) *nvariants = n;
-  for (int v = 0; v < n && v < 8; v++) {
+  for (int v = 0; v < n && v < 16; v++) {
     if (fwd_ms) fwd_ms[v] = C->tune_ms[0][v];
     if (adj_ms) adj_ms[v] = C->tune_ms[1][v];
   }

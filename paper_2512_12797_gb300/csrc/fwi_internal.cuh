@@ -83,6 +83,8 @@ struct StepParams {
   int order3;               // 3D CTA order: 0 tile-major, 1 wavefield-fastest
   int zpair3;               // 3D march: 0 one level at a time, 1 two levels together
   int pair3;                // 3D tiles: 0 one wavefield over 64 x 16, 1 two supergathers over 64 x 8 each
+  int nunits3;              // 3D: wavefield units of the launch (set by launch_step3d)
+  int ctas_per_sm3;         // 3D: persistent grid of this many CTAs per SM (0: one per column)
 };
 
 // Host-side launchers (stencil.cu)

@@ -165,6 +165,8 @@ struct March3D {
   uint64_t* xempty;
   volatile int* abort_flag;
   int lane, ly, lx, x0, y0, gx, gy, b, s, tile, last_q;
+  int zc;                // levels computed by this CTA's warps over all its columns (pair exchange buffers)
+  bool carry;            // after the first column: the previous column's last 4 slots are still held
   int b0, k;             // first wavefield of the CTA, this warp's wavefield index in it
   int xpair;             // pair tiles: index of this warp within its wavefield's group (0-3)
   int acc;               // imaging accumulator of this warp's wavefield (per wavefield or per pair)
@@ -181,6 +183,26 @@ struct March3D {
   float4 Q[NQ], QS[NQ];
   float4 gpend;          // pair tiles, first wavefield's warps: G + q_a L p_a of the previous level
 
+  // Column `it` of the launch (tiles x units, in the order P.order3 picks):
+  // tile-major order runs all tiles of a unit back to back; wavefield-fastest
+  // order runs the tile of every unit side by side, so the supergathers of a
+  // sample read the same cc plane within microseconds of each other (one
+  // DRAM read, the others L2 hits).  A unit is one wavefield, or two (pair
+  // tiles).
+  __device__ __forceinline__ void set_column(int it, int nunits) {
+    const int u = P.order3 ? it % nunits : it / P.ntiles;
+    tile = P.order3 ? it / nunits : it % P.ntiles;
+    b0 = u * S::NWF;
+    b = b0 + k;
+    acc = PAIR ? b0 / 2 : b;
+    x0 = (tile % P.ntx) * TX3;
+    y0 = (tile / P.ntx) * S::TYW;
+    s = b0 / P.nsg;
+    gx = x0 + lx;
+    gy = y0 + ly;
+    colv = gx < L.nxp && gy < L.nyp;
+  }
+
   // Imaging accumulator row of level z (this thread's 4 points).
   __device__ __forceinline__ void store_g(int z, const float4& g) {
     if (!colv) return;
@@ -195,9 +217,10 @@ struct March3D {
   }
 
   // Pair tiles, first wavefield's warps: adds the second wavefield's q L p of
-  // level zp (buffer zp & 1) to gpend and stores the pair's accumulator.
-  __device__ __forceinline__ bool pair_finish(int zp) {
-    const int xb = zp & 1, use = zp >> 1, pr = xpair;
+  // level zp (the CTA's zcp-th computed level: buffer zcp & 1) to gpend and
+  // stores the pair's accumulator.
+  __device__ __forceinline__ bool pair_finish(int zp, int zcp) {
+    const int xb = zcp & 1, use = zcp >> 1, pr = xpair;
     if (!mbar_wait_abortable(&xfull[pr * 2 + xb], (uint32_t)(use & 1), P.status, abort_flag)) return false;
     const float4 cb = ld4s(sm + S::OFF_X + xb * PPLANE + ly * TX3 + lx);
     __syncwarp();
@@ -312,13 +335,14 @@ struct March3D {
         float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (PAIR) {
           // The second wavefield's warp hands q L p of level z to the first's
-          // through buffer z & 1; the first takes it one level later (level
-          // z + 1, or the flush after the last level), so that neither warp
+          // through buffer zc & 1 (zc counts the CTA's computed levels over
+          // all its columns); the first takes it one level later (level z + 1,
+          // or the flush after the column's last level), so that neither warp
           // waits for the other's current level: it keeps G + q_a L p_a of
           // level z in registers until then.
           const int pr = xpair;
           if (k == 1) {
-            const int xb = z & 1, use = z >> 1;
+            const int xb = zc & 1, use = zc >> 1;
             if (use > 0 && !mbar_wait_abortable(&xempty[pr * 2 + xb], (uint32_t)((use - 1) & 1), P.status,
                                                  abort_flag))
               return false;
@@ -329,7 +353,7 @@ struct March3D {
             __syncwarp();
             if (lane == 0) mbar_arrive(&xfull[pr * 2 + xb]);
           } else {
-            if (z > 0 && !pair_finish(z - 1)) return false;
+            if (z > 0 && !pair_finish(z - 1, zc - 1)) return false;
             const float2 g01 = __ffma2_rn(f2(nv[0], nv[1]), f2(lps[0], lps[1]), f2(g.x, g.y));
             const float2 g23 = __ffma2_rn(f2(nv[2], nv[3]), f2(lps[2], lps[3]), f2(g.z, g.w));
             gpend = make_float4(g01.x, g01.y, g23.x, g23.y);
@@ -350,8 +374,10 @@ struct March3D {
         }
       }
     }
+    if (z >= 0) zc++;
     // release the slot of sequence q-4: its halo plane served level q-8 above
-    if (q >= HALO) {
+    // (on a later column, at q < 4: the previous column's last sequences)
+    if (q >= HALO || carry) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[hslot]);
     }
@@ -386,27 +412,13 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.k = warp < NCW3 ? warp / WPG : 0;
   M.xpair = warp % WPG;
   M.ly = 2 * (warp % WPG) + (tid >> 4 & 1);
-  // CTA -> (wavefield unit, tile): tile-major order runs all tiles of a unit
-  // back to back; wavefield-fastest order runs the tile of every unit of the
-  // launch side by side, so the supergathers of a sample read the same cc
-  // plane within microseconds of each other (one DRAM read, the others L2
-  // hits).  A unit is one wavefield, or two (pair tiles).
-  {
-    const int nu = gridDim.x / P.ntiles;
-    const int idx = blockIdx.x;
-    const int u = P.order3 ? idx % nu : idx / P.ntiles;
-    M.tile = P.order3 ? idx / nu : idx % P.ntiles;
-    M.b0 = u * S::NWF;
-  }
-  M.b = M.b0 + M.k;
-  M.acc = PAIR ? M.b0 / 2 : M.b;
-  M.x0 = (M.tile % P.ntx) * TX3;
-  M.y0 = (M.tile / P.ntx) * S::TYW;
-  M.s = M.b0 / P.nsg;
+  // The launch's columns (tiles x units) are dealt to the CTAs in turn: CTA
+  // c runs columns c, c + gridDim.x, ... back to back (a persistent grid of
+  // one CTA per SM), so the TMA ring runs on from one column into the next
+  // instead of draining and refilling at every column.
+  const int nunits = P.nunits3;
+  const int ncols = P.ntiles * nunits;
   M.lx = 4 * (M.lane & 15);
-  M.gx = M.x0 + M.lx;
-  M.gy = M.y0 + M.ly;
-  M.colv = M.gx < L.nxp && M.gy < L.nyp;
   M.last_q = L.nzp + 7;
   M.gz = gz;
   M.pq = 0;
@@ -416,6 +428,8 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   M.lslot = 0;
   M.hslot = S::NST - HALO;  // (0 - 4) mod NST: first used at q = 4
   M.cphase = 0;
+  M.zc = 0;
+  M.carry = false;
 
   if (tid == 0) {
     tma_prefetch_desc(&tm_halo);
@@ -436,16 +450,24 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   if (warp >= NCW3) {  // -------------------------------------------- producer warpgroup
     setmaxnreg_dec<REG3_PRODUCER>();
     if (warp == NCW3 && M.lane == 0) {
-      // sequence q into slot q % NST once every consumer warp has released
-      // sequence q - NST (whose halo plane served level q - NST - 4)
-      while (M.pq <= M.last_q) {
-        if (M.pq >= S::NST &&
-            !mbar_wait_abortable(&empty[M.pst], (uint32_t)((M.pq / S::NST - 1) & 1), P.status, abort_flag))
-          break;
-        M.issue();
+      // sequence g (counted over all columns) into slot g % NST once every
+      // consumer warp has released sequence g - NST (whose halo plane served
+      // the level 4 below it, or, at a column's end, landed last)
+      int gq = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < ncols && ok; it += gridDim.x) {
+        M.set_column(it, nunits);
+        for (M.pq = 0; M.pq <= M.last_q; gq++) {
+          if (gq >= S::NST &&
+              !mbar_wait_abortable(&empty[M.pst], (uint32_t)((gq / S::NST - 1) & 1), P.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          M.issue();
+        }
       }
-      if (M.pq <= M.last_q) {  // gave up: bounded wait for the copies in flight
-        for (int i = M.pq - S::NST > 0 ? M.pq - S::NST : 0; i < M.pq; i++) {
+      if (!ok) {  // gave up: bounded wait for the copies in flight
+        for (int i = gq - S::NST > 0 ? gq - S::NST : 0; i < gq; i++) {
           const long long t0 = clock64();
           while (!mbar_try_wait(&full[i % S::NST], (uint32_t)((i / S::NST) & 1)) && clock64() - t0 < (1LL << 24)) {
           }
@@ -456,20 +478,6 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   }
   setmaxnreg_inc<REG3_CONSUMER>();
 
-  M.gyv = M.gy < L.nyp ? __ldg(P.gtab + L.nzp + M.gy) : 0.f;
-#pragma unroll
-  for (int j = 0; j < 4; j++) M.gxv[j] = M.gx + j < L.nxp ? __ldg(P.gtab + L.nzp + L.nyp + M.gx + j) : 0.f;
-  M.ie_cur = P.inj_off[M.b * P.inj_bstride + M.tile];
-  M.ie_end = P.inj_off[M.b * P.inj_bstride + M.tile + 1];
-  M.se_cur = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile] : 0;
-  M.se_end = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile + 1] : 0;
-  M.inj_z = M.ie_cur < M.ie_end ? P.inj[M.ie_cur].w : 0x7fffffff;
-  M.smp_z = M.se_cur < M.se_end ? P.smp4[M.se_cur].z : 0x7fffffff;
-#pragma unroll
-  for (int i = 0; i < NQ; i++) {
-    M.Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    M.QS[i] = M.Q[i];
-  }
   // Sequence q lands at queue index q % NQ (the centre of level q - 4) and
   // level q - 8 has its centre at (q - 4) % NQ.  NQ = 9: one sequence, one
   // level at a time.  NQ = 10: two sequences land, then their two levels are
@@ -483,35 +491,53 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   if (!M.template land<(k) + 1>()) return;                  \
   if (!M.template level<((k) + 6) % 10>(q + (k))) return;   \
   if (!M.template level<((k) + 7) % 10>(q + (k) + 1)) return;
-  int q = 0;
-  if constexpr (NQ == 9) {
-    for (; q + 9 <= M.last_q + 1; q += 9) {
-      FWI_ONE(0) FWI_ONE(1) FWI_ONE(2) FWI_ONE(3) FWI_ONE(4) FWI_ONE(5) FWI_ONE(6) FWI_ONE(7) FWI_ONE(8)
+  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+    M.set_column(it, nunits);
+    M.gyv = M.gy < L.nyp ? __ldg(P.gtab + L.nzp + M.gy) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++) M.gxv[j] = M.gx + j < L.nxp ? __ldg(P.gtab + L.nzp + L.nyp + M.gx + j) : 0.f;
+    M.ie_cur = P.inj_off[M.b * P.inj_bstride + M.tile];
+    M.ie_end = P.inj_off[M.b * P.inj_bstride + M.tile + 1];
+    M.se_cur = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile] : 0;
+    M.se_end = P.smp4 ? P.smp_off[M.b * P.smp_bstride + M.tile + 1] : 0;
+    M.inj_z = M.ie_cur < M.ie_end ? P.inj[M.ie_cur].w : 0x7fffffff;
+    M.smp_z = M.se_cur < M.se_end ? P.smp4[M.se_cur].z : 0x7fffffff;
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+      M.Q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      M.QS[i] = M.Q[i];
     }
-    const int rem = M.last_q + 1 - q;
-    if (rem > 0) { FWI_ONE(0) }
-    if (rem > 1) { FWI_ONE(1) }
-    if (rem > 2) { FWI_ONE(2) }
-    if (rem > 3) { FWI_ONE(3) }
-    if (rem > 4) { FWI_ONE(4) }
-    if (rem > 5) { FWI_ONE(5) }
-    if (rem > 6) { FWI_ONE(6) }
-    if (rem > 7) { FWI_ONE(7) }
-  } else {
-    for (; q + 10 <= M.last_q + 1; q += 10) {
-      FWI_TWO(0) FWI_TWO(2) FWI_TWO(4) FWI_TWO(6) FWI_TWO(8)
+    int q = 0;
+    if constexpr (NQ == 9) {
+      for (; q + 9 <= M.last_q + 1; q += 9) {
+        FWI_ONE(0) FWI_ONE(1) FWI_ONE(2) FWI_ONE(3) FWI_ONE(4) FWI_ONE(5) FWI_ONE(6) FWI_ONE(7) FWI_ONE(8)
+      }
+      const int rem = M.last_q + 1 - q;
+      if (rem > 0) { FWI_ONE(0) }
+      if (rem > 1) { FWI_ONE(1) }
+      if (rem > 2) { FWI_ONE(2) }
+      if (rem > 3) { FWI_ONE(3) }
+      if (rem > 4) { FWI_ONE(4) }
+      if (rem > 5) { FWI_ONE(5) }
+      if (rem > 6) { FWI_ONE(6) }
+      if (rem > 7) { FWI_ONE(7) }
+    } else {
+      for (; q + 10 <= M.last_q + 1; q += 10) {
+        FWI_TWO(0) FWI_TWO(2) FWI_TWO(4) FWI_TWO(6) FWI_TWO(8)
+      }
+      const int rem = M.last_q + 1 - q;
+      if (rem >= 2) { FWI_TWO(0) } else if (rem == 1) { FWI_ONE(0) }
+      if (rem >= 4) { FWI_TWO(2) } else if (rem == 3) { FWI_ONE(2) }
+      if (rem >= 6) { FWI_TWO(4) } else if (rem == 5) { FWI_ONE(4) }
+      if (rem >= 8) { FWI_TWO(6) } else if (rem == 7) { FWI_ONE(6) }
+      if (rem == 9) { FWI_ONE(8) }
     }
-    const int rem = M.last_q + 1 - q;
-    if (rem >= 2) { FWI_TWO(0) } else if (rem == 1) { FWI_ONE(0) }
-    if (rem >= 4) { FWI_TWO(2) } else if (rem == 3) { FWI_ONE(2) }
-    if (rem >= 6) { FWI_TWO(4) } else if (rem == 5) { FWI_ONE(4) }
-    if (rem >= 8) { FWI_TWO(6) } else if (rem == 7) { FWI_ONE(6) }
-    if (rem == 9) { FWI_ONE(8) }
+    // pair tiles: the first wavefield's warps still hold the column's last level
+    if (ADJ && PAIR && M.k == 0 && !M.pair_finish(L.nzp - 1, M.zc - 1)) return;
+    M.carry = true;
   }
 #undef FWI_ONE
 #undef FWI_TWO
-  // pair tiles: the first wavefield's warps still hold the last level
-  if (ADJ && PAIR && M.k == 0 && L.nzp > 0) M.pair_finish(L.nzp - 1);
 }
 
 template <bool ADJ, bool ISO, bool PAIR>
@@ -529,22 +555,34 @@ static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_pla
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
                           const CUtensorMap& tm_g, const Layout& L, const Coef& K, const StepParams& P, int B,
                           cudaStream_t st) {
-  // grid: tiles x units (one wavefield, or a pair of supergathers of one sample)
+  // columns: tiles x units (one wavefield, or a pair of supergathers of one
+  // sample), dealt in turn to a persistent grid of at most one CTA per SM
   if (P.pair3 && (B % 2 || P.nsg % 2)) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)(P.ntiles * (P.pair3 ? B / 2 : B)));
+  StepParams Q = P;
+  Q.nunits3 = P.pair3 ? B / 2 : B;
+  const long long ncols = (long long)P.ntiles * Q.nunits3;
+  static int nsm = 0;
+  if (nsm <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm <= 0)
+      nsm = 1;
+  }
+  const long long cap = (long long)nsm * P.ctas_per_sm3;
+  dim3 grid((unsigned)(P.ctas_per_sm3 > 0 && ncols > cap ? cap : ncols));
   // The one-bracket form serves the forward only: on the layered 3D batch
   // it made the forward step 4 % faster and the adjoint step (two
   // Laplacians) 2 % slower.
   if (adj)
-    return P.pair3 ? launch3<true, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
-                   : launch3<true, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+    return P.pair3 ? launch3<true, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
+                   : launch3<true, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
   bool iso = true;
   for (int k = 1; k <= 4; k++) iso = iso && K.cx[k] == K.cy[k] && K.cx[k] == K.cz[k];
   if (P.pair3)
-    return iso ? launch3<false, true, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
-               : launch3<false, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
-  return iso ? launch3<false, true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st)
-             : launch3<false, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P, grid, st);
+    return iso ? launch3<false, true, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
+               : launch3<false, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
+  return iso ? launch3<false, true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
+             : launch3<false, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
 }
 
 }  // namespace fwi

@@ -171,7 +171,9 @@ def test_3d_step_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3)):  # adjoint on 64 x 16 tiles
+    # adjoint on 64 x 16 tiles; bit 3: persistent grid
+    for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3), (11, 9), (12, 10), (15, 11),
+                (8, 8)):
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
         m, g = ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0)
@@ -179,8 +181,8 @@ def test_3d_step_variants_bit_identical(P):
         out.append((m, g, rec))
         got = ctx.variants()
         assert (got["forward"], got["adjoint"]) == var
-        if var[0] >= 4:
-            assert "pairs" in got["forward_name"]
+        assert ("pairs" in got["forward_name"]) == bool(var[0] & 4)
+        assert ("persistent" in got["forward_name"]) == bool(var[0] & 8)
         ctx.close()
     torch.cuda.synchronize()
     for m, g, rec in out[1:]:
@@ -200,15 +202,15 @@ def test_3d_pair_tile_adjoint_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    for var in ((3, 4), (0, 5), (1, 6), (2, 7), (3, 0)):
+    for var in ((3, 4), (0, 5), (1, 6), (2, 7), (11, 12), (3, 13), (3, 0)):
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
         out.append(ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0))
-        assert ("pairs" in ctx.variants()["adjoint_name"]) == (var[1] >= 4)
+        assert ("pairs" in ctx.variants()["adjoint_name"]) == bool(var[1] & 4)
         ctx.close()
     torch.cuda.synchronize()
-    for m, g in out[1:4]:
+    for m, g in out[1:6]:
         assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0])
-    m0, g0 = out[4]
+    m0, g0 = out[6]
     assert torch.equal(m0, out[0][0])
     assert float((g0 - out[0][1]).norm() / g0.norm()) < 1e-6
