@@ -347,9 +347,10 @@ def gradient_run(P, torch, w, steps, warmup, e2e_steps, dist, dev, world, rank, 
     h2d = vel_h.numel() * 4 + dobs_h.numel() * 4
     d2h = out_h.numel() * 4 + nsamp * 8
 
-    # roofline of the dominant step kernel from the per-phase events.  In 2D one
-    # launch runs all steps of a phase (forward: nt steps; adjoint: the steps of a
-    # checkpoint segment), in 3D every step is a launch; both are charged per step.
+    # roofline of the dominant step kernel from the per-phase events.  A
+    # multi-step launch (2D; the persistent 3D variants) runs all steps of a
+    # phase (forward: nt steps; adjoint: the steps of a checkpoint segment),
+    # otherwise every step is a launch; both are charged per step.
     bpu = bytes_per_update(nsg, w.ndim, "pairs" in var["forward_name"], "pairs" in var["adjoint_name"])
     nchunks = (nsamp + plan["samples_per_chunk"] - 1) // plan["samples_per_chunk"]
     fwd_steps = w.nt * nchunks * steps
@@ -385,8 +386,10 @@ def gradient_run(P, torch, w, steps, warmup, e2e_steps, dist, dev, world, rank, 
                 "point_updates_per_step": per_step_pts,
                 "avg_step_ms": kern[dom]["ms"],
                 "share_of_step": kern[dom]["share"],
-                "steps_per_launch": ({"forward": w.nt, "adjoint": min(plan["segment_len"], w.nt)}
-                                     if w.ndim == 2 else {"forward": 1, "adjoint": 1}),
+                "steps_per_launch": {
+                    "forward": w.nt if w.ndim == 2 or "multi-step" in var["forward_name"] else 1,
+                    "adjoint": (min(plan["segment_len"], w.nt)
+                                if w.ndim == 2 or "multi-step" in var["adjoint_name"] else 1)},
                 "other_kernel": {"name": other, "achieved": other_gbs, "frac": other_gbs / peak,
                                  "avg_step_ms": kern[other]["ms"], "share_of_step": kern[other]["share"]}}
     res = {"value": value, "ms": ms, "clocks": clk, "units": units, "plan": plan, "variants": var,

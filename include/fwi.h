@@ -322,7 +322,11 @@ int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
  *          one imaging accumulator per pair), when a sample has an even
  *          number of supergathers;
  *   bit 3  one CTA per column, or a persistent grid of one CTA per SM that
- *          runs its columns back to back.
+ *          runs its columns back to back;
+ *   bit 4  (with bit 3) one launch per time step, or all steps of a phase in
+ *          one cooperative launch, a column's step starting once its 3 x 3
+ *          tile neighbourhood has finished the step before (progress flags
+ *          in device memory); bit 4 without bit 3 is rejected.
  * By default the first fwi_forward / fwi_gradient call for a given
  * (nsamp*nsg, nsg) times every variant on that shape (synchronising the stream
  * while it does) and keeps the fastest; the variants it chooses among give
@@ -330,7 +334,8 @@ int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
  * the pair form sums the imaging term in another order, so it is used only
  * when forced.  fwi_set_kernel_variants forces a variant index (-1 restores
  * autotuning; FWI_ERR_ARG beyond the variant count); fwi_kernel_variants
- * reports the chosen indices and names and, in ms[0..15], the per-step time
+ * reports the chosen indices and names and, in ms[0..31] (2D: the first
+ * nvariants), the per-step time
  * of each variant measured by the tuner (-1: not run). */
 int fwi_set_kernel_variants(fwi_ctx* ctx, int fwd, int adj);
 int fwi_kernel_variants(fwi_ctx* ctx, int* fwd, int* adj, const char** fwd_name, const char** adj_name,

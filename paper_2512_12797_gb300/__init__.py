@@ -201,7 +201,7 @@ class FWI:
     def variants(self):
         f, a, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         fn, an = ctypes.c_char_p(), ctypes.c_char_p()
-        fm, am = (ctypes.c_float * 16)(), (ctypes.c_float * 16)()
+        fm, am = (ctypes.c_float * 32)(), (ctypes.c_float * 32)()
         check(lib().fwi_kernel_variants(self._h, ctypes.byref(f), ctypes.byref(a), ctypes.byref(fn), ctypes.byref(an),
                                         fm, am, ctypes.byref(n)), "fwi_kernel_variants")
         return {"forward": f.value, "adjoint": a.value, "forward_name": (fn.value or b"").decode(),

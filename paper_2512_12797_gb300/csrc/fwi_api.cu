@@ -111,6 +111,9 @@ bool make_plan(int nt, long long avail, Plan* out) {
 }
 
 constexpr int kTuneSteps = 6;  // steps per autotuner timing launch
+constexpr int kMaxVariants = 32;  // step-kernel variants per direction (3D: five bits)
+// 3D variant v runs all steps of a phase in one launch (bits 3 and 4 set)
+inline bool multi_step3(int v) { return (v & 24) == 24; }
 // Pinned staging buffers per kind (point lists, step descriptors), used in
 // turn: an upload waits only for the copy issued kStaging uploads earlier,
 // so the host can run that many gradient chunks ahead of the device before
@@ -199,7 +202,7 @@ struct fwi_ctx {
   int forced[2] = {-1, -1};
   int tuned_B = -1, tuned_nsg = -1;  // call shape the variants were tuned for
   int adj_pair = 0;  // tile shape of the 3D adjoint in the last tuned call (shape_adj)
-  float tune_ms[2][16] = {};
+  float tune_ms[2][kMaxVariants] = {};
   int* zero_off = nullptr;  // [ntiles+1] zeros: "no points in any tile"
   float* gtab = nullptr;    // gamma*dt per axis: z [nzp], y [nyp], x [nxp]
   // step descriptors of the current call, in launch order (device, pinned
@@ -540,13 +543,28 @@ StepParams base_params(fwi_ctx* C, int B, int nsg, int sh = 0) {
 }
 
 // Steps descs[off, off + n) of the current call: one multi-step launch in 2D
-// (progress flags zeroed first), one launch per step in 3D.
-// P carries its tile shape (P.pair3) and that shape's lists.
+// and for the persistent 3D variants (progress flags zeroed first), else one
+// launch per step.  P carries its tile shape (P.pair3) and that shape's lists.
 int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int B, const Maps& M, cudaStream_t st,
               long long* launches) {
   if (n <= 0) return FWI_OK;
   const int sh = P.pair3;
   if (C->L.ndim == 3) {
+    const int v = C->var[adj ? 1 : 0];
+    P.order3 = v & 1;
+    P.zpair3 = (v >> 1) & 1;
+    P.ctas_per_sm3 = (v >> 3) & 1;
+    if (multi_step3(v)) {
+      const int units = sh ? B / 2 : B;
+      P.steps = C->desc + off;
+      P.nsteps = n;
+      P.done = C->done;
+      CK(cudaMemsetAsync(C->done, 0, (size_t)units * P.ntiles * 4, st));
+      CK(launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st));
+      *launches += 1;
+      return FWI_OK;
+    }
+    P.steps = nullptr;
     for (int i = 0; i < n; i++) {
       const StepDesc& d = C->descs[off + i];
       P.s_cur = d.cur;
@@ -554,9 +572,6 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
       P.s_out = d.out;
       P.s_snap = d.snap;
       P.t = d.t;
-      P.order3 = C->var[adj ? 1 : 0] & 1;
-      P.zpair3 = (C->var[adj ? 1 : 0] >> 1) & 1;
-      P.ctas_per_sm3 = (C->var[adj ? 1 : 0] >> 3) & 1;
       CK(launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st));
     }
     *launches += n;
@@ -600,27 +615,30 @@ StepDesc make_desc(int cur, int prev, int out, int snap, int t) {
 // step, bit 2 the tile shape (64 x 16, or 64 x 8 pair tiles when a sample
 // has an even number of supergathers; for the adjoint only when forced, see
 // shape_adj), bit 3 a persistent grid of one CTA per SM running its columns
-// back to back (else one CTA per column).
-int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? 16 : num_variants2d(adj); }
+// back to back (else one CTA per column), bit 4 (with bit 3) all steps of a
+// phase in one cooperative launch, chained column by column by progress
+// flags (else one launch per step).  Bit 4 without bit 3 is not a variant.
+int num_variants(const fwi_ctx* C, bool adj) { return C->L.ndim == 3 ? kMaxVariants : num_variants2d(adj); }
 const char* variant_name(const fwi_ctx* C, bool adj, int v) {
   if (C->L.ndim == 2) return variant2d_name(adj, v);
-  static char names[2][16][64];
+  static char names[2][kMaxVariants][96];
   static bool init = false;
   if (!init) {
     for (int a = 0; a < 2; a++)
-      for (int i = 0; i < 16; i++)
-        snprintf(names[a][i], sizeof(names[a][i]), "%s %s %s, %d level%s%s", a ? "adj3d" : "fwd3d",
+      for (int i = 0; i < kMaxVariants; i++)
+        snprintf(names[a][i], sizeof(names[a][i]), "%s %s %s, %d level%s%s%s", a ? "adj3d" : "fwd3d",
                  (i & 4) ? "64x8 pairs" : "64x16", (i & 1) ? "wavefield-fastest" : "tile-major", (i & 2) ? 2 : 1,
-                 (i & 2) ? "s" : "", (i & 8) ? ", persistent" : "");
+                 (i & 2) ? "s" : "", (i & 8) ? ", persistent" : "", multi_step3(i) ? " multi-step" : "");
     init = true;
   }
-  if (v < 0 || v > 15) return "-";
+  if (v < 0 || v >= kMaxVariants || ((v & 16) && !(v & 8))) return "-";
   if (adj && C->adj_pair != ((v >> 2) & 1)) return names[1][v ^ 4];  // the shape the adjoint ran on
   return names[adj ? 1 : 0][v];
 }
 
-// kTuneSteps steps of variant v: one multi-step launch in 2D, one launch per
-// step in 3D (slots from td).  P carries the variant's tile shape and lists.
+// kTuneSteps steps of variant v: one multi-step launch in 2D and for the
+// persistent 3D variants (step table P.steps), else one launch per step
+// (slots from td).  P carries the variant's tile shape and lists.
 cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDesc* td, int nsamp, int B,
                         const Maps& M, cudaStream_t st) {
   if (C->L.ndim == 3) {
@@ -628,6 +646,12 @@ cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDes
     P.zpair3 = (v >> 1) & 1;
     P.ctas_per_sm3 = (v >> 3) & 1;
     const int sh = P.pair3;
+    if (multi_step3(v)) {
+      cudaError_t e = cudaMemsetAsync(C->done, 0, (size_t)(sh ? B / 2 : B) * P.ntiles * 4, st);
+      if (e != cudaSuccess) return e;
+      return launch_step3d(adj, M.th[sh], M.tp[sh], M.tc[sh], M.tg[sh], C->L, C->K, P, B, st);
+    }
+    P.steps = nullptr;
     for (int i = 0; i < kTuneSteps; i++) {
       P.s_cur = td[i].cur;
       P.s_prev = td[i].prev;
@@ -670,7 +694,7 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cu
   CK(cudaEventCreate(&e1));
   for (int adj = 0; adj < 2; adj++) {
     const int nv = num_variants(C, adj != 0);
-    for (int v = 0; v < 16; v++) C->tune_ms[adj][v] = -1.f;
+    for (int v = 0; v < kMaxVariants; v++) C->tune_ms[adj][v] = -1.f;
     if (C->forced[adj] >= 0 && C->forced[adj] < nv) {
       // a forced 3D pair-tile forward needs an even number of supergathers:
       // otherwise the same variant with 64 x 16 tiles
@@ -679,8 +703,9 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cu
     }
     int best = -1;
     float best_ms = 1e30f;
-    for (int v = 0; v < nv && v < 16; v++) {
+    for (int v = 0; v < nv && v < kMaxVariants; v++) {
       if (C->L.ndim == 3 && adj && (v & 4)) continue;  // the adjoint's tile shape is not tuned (shape_adj)
+      if (C->L.ndim == 3 && (v & 16) && !(v & 8)) continue;  // multi-step needs the persistent grid
       // pair tiles need an even number of supergathers per sample
       const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : 0;
       if (sh && nsg % 2) continue;
@@ -1196,9 +1221,10 @@ static int gradient_calls(fwi_ctx* C, const float* vel, int nsamp, const int32_t
   // nsg supergathers (~1.7 us per tile), but at least ~15 us: with about one
   // item per CTA each step waits for its neighbours' previous one (flag,
   // fence, poll, TMA latency); plus ~20 us per launch (three per checkpoint
-  // segment).  In 3D every step is a launch of at least ~8 us that runs
-  // ceil(CTAs / SMs) waves of equal CTAs (one CTA per SM), each CTA a column
-  // of TX3 x TY3 x nzp points at ~16 B per point from a ~6 TB/s share.
+  // segment).  In 3D a step (a launch of at least ~8 us, or one step of a
+  // multi-step launch) runs ceil(CTAs / SMs) waves of equal CTAs (one CTA
+  // per SM), each CTA a column of TX3 x TY3 x nzp points at ~16 B per point
+  // from a ~6 TB/s share.
   int nsm = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm <= 0) nsm = 1;
@@ -1377,6 +1403,8 @@ int fwi_plan_info(fwi_ctx* C, int* K, int* nseg, int64_t* rec, int* used, int* a
 int fwi_set_kernel_variants(fwi_ctx* C, int fwd, int adj) {
   if (!C) return FWI_ERR_ARG;
   if (fwd >= num_variants(C, false) || adj >= num_variants(C, true)) return FWI_ERR_ARG;
+  if (C->L.ndim == 3 && ((fwd >= 0 && (fwd & 16) && !(fwd & 8)) || (adj >= 0 && (adj & 16) && !(adj & 8))))
+    return FWI_ERR_ARG;  // multi-step (bit 4) needs the persistent grid (bit 3)
   C->forced[0] = fwd < 0 ? -1 : fwd;
   C->forced[1] = adj < 0 ? -1 : adj;
   C->tuned_B = -1;
@@ -1392,7 +1420,7 @@ int fwi_kernel_variants(fwi_ctx* C, int* fwd, int* adj, const char** fwd_name, c
   if (adj_name) *adj_name = variant_name(C, true, C->var[1]);
   const int n = std::max(num_variants(C, false), num_variants(C, true));
   if (nvariants) *nvariants = n;
-  for (int v = 0; v < n && v < 16; v++) {
+  for (int v = 0; v < n && v < kMaxVariants; v++) {
     if (fwd_ms) fwd_ms[v] = C->tune_ms[0][v];
     if (adj_ms) adj_ms[v] = C->tune_ms[1][v];
   }

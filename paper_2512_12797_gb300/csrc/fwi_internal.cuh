@@ -76,8 +76,10 @@ struct StepParams {
   const int4* smp4;         // {local, col, z, 0}                (3D; inj .w holds z)
   float* smp_out; long long smp_bstride_out; int smp_ld;
   int* status;
-  // multi-step launches (2D): step descriptors and per-item progress flags
-  // (item = tile of one sample, flag = steps completed; zero at launch)
+  // multi-step launches (2D; 3D persistent variants): step descriptors and
+  // per-item progress flags (item = tile of one sample in 2D, of one unit in
+  // 3D; flag = steps completed; zero at launch).  3D: steps == nullptr for a
+  // one-step launch that takes its slots and t from the fields above.
   const StepDesc* steps; int nsteps;
   int* done;
   int order3;               // 3D CTA order: 0 tile-major, 1 wavefield-fastest

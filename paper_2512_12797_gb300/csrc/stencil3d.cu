@@ -42,6 +42,7 @@ namespace fwi {
 constexpr int NCW3 = TY3 / 2;        // consumer warps (two y rows each)
 constexpr int NTHREADS3 = 32 * NCW3 + 128;  // + producer warpgroup
 constexpr int REG3_LAUNCH = 168, REG3_PRODUCER = 72, REG3_CONSUMER = 216;
+constexpr int WDONE3 = 8;            // column-completion counters (ring), multi-step launches
 static_assert(128 * REG3_PRODUCER + 32 * NCW3 * REG3_CONSUMER <= NTHREADS3 * REG3_LAUNCH,
               "register split exceeds the launch allocation");
 
@@ -66,7 +67,8 @@ struct Smem3D {
   static constexpr int OFF_GZ = OFF_X + (ADJ && PAIR ? 2 * PPLANE : 0);  // gamma*dt of every z level
   static constexpr int NXB = ADJ && PAIR ? 16 : 0;  // exchange barriers: full[4][2], empty[4][2]
   static size_t bytes(int nzp) {
-    return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + (2 * NST + NXB) * 8 + 16;
+    // + abort word, dependency counter, column-completion counters
+    return ((size_t)OFF_GZ + ((nzp + 31) / 32) * 32) * 4 + (2 * NST + NXB) * 8 + (2 + WDONE3) * 4 + 8;
   }
   static_assert((PLANE * 4) % 128 == 0 && (PPLANE * 4) % 128 == 0 && (STAGE * 4) % 128 == 0,
                 "stage parts must stay 128-byte aligned");
@@ -146,6 +148,64 @@ __device__ __forceinline__ void lap3(const float* __restrict__ H, const float4 (
   }
 }
 
+// Column `it` of a launch -> (unit, tile) in the CTA order P.order3 picks:
+// tile-major order runs all tiles of a unit back to back; wavefield-fastest
+// order runs the tile of every unit side by side.
+__device__ __forceinline__ void column_of(const StepParams& P, int it, int nunits, int& u, int& tile) {
+  u = P.order3 ? it % nunits : it / P.ntiles;
+  tile = P.order3 ? it / nunits : it % P.ntiles;
+}
+
+// Multi-step launches: bounded poll of the progress flags of the 3 x 3 tile
+// neighbourhood of column (u, tile) until each has completed `need` steps,
+// then acquire-orders the neighbours' stores before the TMA loads that
+// follow.  Gives up on timeout, on the CTA's abort word, or when another CTA
+// has recorded an error.
+// (The fields of the launch's StepParams come by value: a reference to the
+// kernel parameter would give every thread a local copy of it.)
+__device__ __noinline__ bool wait_columns3(const int* done, int ntx, int ntiles, int* status, int u, int tile,
+                                           int need, volatile int* abort_flag) {
+  const int tx = tile % ntx, ty = tile / ntx, nty = ntiles / ntx;
+  const int* base = done + (long long)u * ntiles;
+  const int y_lo = max(ty - 1, 0), y_hi = min(ty + 1, nty - 1);
+  const int x_lo = max(tx - 1, 0), x_hi = min(tx + 1, ntx - 1);
+  const long long t0 = clock64();
+  for (;;) {
+    int lo = need;
+    for (int y = y_lo; y <= y_hi; y++)
+      for (int x = x_lo; x <= x_hi; x++) lo = min(lo, ld_relaxed_gpu(base + y * ntx + x));
+    if (lo >= need) break;
+    if (*abort_flag || ld_relaxed_gpu(status) != 0) {
+      *abort_flag = 1;
+      return false;
+    }
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(status, 0, (int)FWI_ERR_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+    __nanosleep(128);
+  }
+  fence_acq_rel_gpu();
+  fence_proxy_async_global();
+  return true;
+}
+
+// Bounded wait until the shared counter *c exceeds v (acquire at CTA scope).
+__device__ __forceinline__ bool wait_counter(const int* c, int v, int* status, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (ld_acquire_cta_shared(c) <= v) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(status, 0, (int)FWI_ERR_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
 template <bool ADJ, bool ISO, int NQ, bool PAIR>
 struct March3D {
   using S = Smem3D<ADJ, PAIR>;
@@ -168,6 +228,7 @@ struct March3D {
   int zc;                // levels computed by this CTA's warps over all its columns (pair exchange buffers)
   bool carry;            // after the first column: the previous column's last 4 slots are still held
   int b0, k;             // first wavefield of the CTA, this warp's wavefield index in it
+  int s_cur, s_prev, s_out, s_snap, t;  // slots and record time of the current step
   int xpair;             // pair tiles: index of this warp within its wavefield's group (0-3)
   int acc;               // imaging accumulator of this warp's wavefield (per wavefield or per pair)
   bool colv;
@@ -183,15 +244,32 @@ struct March3D {
   float4 Q[NQ], QS[NQ];
   float4 gpend;          // pair tiles, first wavefield's warps: G + q_a L p_a of the previous level
 
-  // Column `it` of the launch (tiles x units, in the order P.order3 picks):
-  // tile-major order runs all tiles of a unit back to back; wavefield-fastest
-  // order runs the tile of every unit side by side, so the supergathers of a
-  // sample read the same cc plane within microseconds of each other (one
-  // DRAM read, the others L2 hits).  A unit is one wavefield, or two (pair
-  // tiles).
+  // Slots and record time of step n of the launch: from the step table of a
+  // multi-step launch, else from P (one step).
+  __device__ __forceinline__ void set_step(int n) {
+    if (P.steps) {
+      const int4 d = __ldg(reinterpret_cast<const int4*>(P.steps + n));
+      s_cur = d.x;
+      s_prev = d.y;
+      s_out = d.z;
+      s_snap = d.w;
+      t = __ldg(&P.steps[n].t);
+    } else {
+      s_cur = P.s_cur;
+      s_prev = P.s_prev;
+      s_out = P.s_out;
+      s_snap = P.s_snap;
+      t = P.t;
+    }
+  }
+
+  // Column `it` of the launch (tiles x units).  In wavefield-fastest order
+  // the supergathers of a sample read the same cc plane within microseconds
+  // of each other (one DRAM read, the others L2 hits).  A unit is one
+  // wavefield, or two (pair tiles).
   __device__ __forceinline__ void set_column(int it, int nunits) {
-    const int u = P.order3 ? it % nunits : it / P.ntiles;
-    tile = P.order3 ? it / nunits : it % P.ntiles;
+    int u;
+    column_of(P, it, nunits, u, tile);
     b0 = u * S::NWF;
     b = b0 + k;
     acc = PAIR ? b0 / 2 : b;
@@ -240,13 +318,13 @@ struct March3D {
     mbar_arrive_expect_tx(&full[pst], bytes);
 #pragma unroll
     for (int w = 0; w < S::NWF; w++) {
-      tma_load_5d(base + w * PLANE, th, x0, y0, zh + HALO, b0 + w, P.s_cur, &full[pst]);
-      if (ADJ) tma_load_5d(base + S::OFF_SNAP + w * PLANE, th, x0, y0, zh + HALO, b0 + w, P.s_snap, &full[pst]);
+      tma_load_5d(base + w * PLANE, th, x0, y0, zh + HALO, b0 + w, s_cur, &full[pst]);
+      if (ADJ) tma_load_5d(base + S::OFF_SNAP + w * PLANE, th, x0, y0, zh + HALO, b0 + w, s_snap, &full[pst]);
     }
     if (plain) {
 #pragma unroll
       for (int w = 0; w < S::NWF; w++)
-        tma_load_5d(base + S::OFF_PREV + w * PPLANE, tp, x0 + HALO, y0 + HALO, zp + HALO, b0 + w, P.s_prev,
+        tma_load_5d(base + S::OFF_PREV + w * PPLANE, tp, x0 + HALO, y0 + HALO, zp + HALO, b0 + w, s_prev,
                     &full[pst]);
       tma_load_4d(base + S::OFF_CC, tcc, x0 + HALO, y0 + HALO, zp + HALO, s, &full[pst]);
       if (ADJ) tma_load_4d(base + S::OFF_G, tg, x0 + HALO, y0 + HALO, zp + HALO, PAIR ? b0 / 2 : b0, &full[pst]);
@@ -271,6 +349,75 @@ struct March3D {
     return true;
   }
 
+  // p^{n+1} (forward) or q^k (adjoint) at the thread's 4 points of level z,
+  // from the halo plane hpl of level z (queue centre at index C) and the
+  // plain planes of stage: cc * L p + (p + b (p - pm)).  No side effects.
+  template <int C>
+  __device__ __forceinline__ void advance(int z, const float* hpl, const float* stage, float (&nv)[4]) const {
+    float lap[4];
+    lap3<C, ISO, NQ>(hpl, Q, ly, lx, K, lap);
+    const float4 pm = ld4s(stage + S::OFF_PREV + k * PPLANE + ly * TX3 + lx);
+    const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
+    const float gzy = gz[z] + gyv;
+#pragma unroll
+    for (int j = 0; j < 4; j += 2) {  // in pairs
+      const float2 bb = f2(sponge_b(gzy + gxv[j]), sponge_b(gzy + gxv[j + 1]));
+      const float2 p = half2of(Q[C % NQ], j);
+      const float2 d = __ffma2_rn(half2of(pm, j), f2(-1.f, -1.f), p);
+      const float2 n2 = __ffma2_rn(half2of(cv, j), f2(lap[j], lap[j + 1]), __ffma2_rn(bb, d, p));
+      nv[j] = n2.x;
+      nv[j + 1] = n2.y;
+    }
+  }
+
+  // Injection / sampling at level z: staged in this warp's two rows of the
+  // p^{n-1} plane of stage (already consumed); entry .x is the point's index
+  // in that plane, and its row / 2 names the warp that owns it.
+  __device__ __forceinline__ void inject(int z, float* stage, float (&nv)[4]) {
+    if (inj_z != z && smp_z != z) return;
+    float* pl = stage + S::OFF_PREV + k * PPLANE;
+    const int wrow = ly >> 1;
+    __syncwarp();
+    *reinterpret_cast<float4*>(pl + ly * TX3 + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+    __syncwarp();
+    int e_end = ie_cur;
+    while (e_end < ie_end && P.inj[e_end].w == z) e_end++;
+    for (int e = ie_cur + lane; e < e_end; e += 32) {
+      const int4 en = P.inj[e];
+      if ((en.x / TX3) >> 1 != wrow) continue;
+      const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + en.x / TX3, x0 + en.x % TX3));
+      pl[en.x] += ccp * (__int_as_float(en.z) *
+                         P.series[(long long)b * P.series_bstride + (long long)t * P.series_ld + en.y]);
+    }
+    ie_cur = e_end;
+    inj_z = ie_cur < ie_end ? P.inj[ie_cur].w : 0x7fffffff;
+    __syncwarp();
+    const float4 v = ld4s(pl + ly * TX3 + lx);
+    nv[0] = v.x; nv[1] = v.y; nv[2] = v.z; nv[3] = v.w;
+    int s_end = se_cur;
+    while (s_end < se_end && P.smp4[s_end].z == z) s_end++;
+    for (int e = se_cur + lane; e < s_end; e += 32) {
+      const int4 en = P.smp4[e];
+      if ((en.x / TX3) >> 1 != wrow) continue;
+      P.smp_out[(long long)b * P.smp_bstride_out + (long long)t * P.smp_ld + en.y] = pl[en.x];
+    }
+    se_cur = s_end;
+    smp_z = se_cur < se_end ? P.smp4[se_cur].z : 0x7fffffff;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+
+  // The new wavefield's row of level z (this thread's 4 points).
+  __device__ __forceinline__ void store_p(int z, const float (&nv)[4]) {
+    if (!colv) return;
+    float* o = P.pool + (long long)s_out * P.slot_elems + (long long)b * L.field + L.off(z, gy, gx);
+    if (gx + 3 < L.nxp) {
+      *reinterpret_cast<float4*>(o) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+    } else {
+      for (int j = 0; j < 4; j++)
+        if (gx + j < L.nxp) o[j] = nv[j];
+    }
+  }
+
   // Level z = q - 8 from landed sequences q (plain planes) and q - 4 (halo
   // plane), queue centre at compile-time index C = (q - 4) % NQ; then the
   // slot of sequence q - 4 is released.
@@ -280,55 +427,9 @@ struct March3D {
     const int z = q - 2 * HALO;
     if (z >= 0) {
       const float* hpl = sm + hslot * S::STAGE + k * PLANE;  // halo plane of level z (sequence q - 4)
-      float lap[4];
-      lap3<C, ISO, NQ>(hpl, Q, ly, lx, K, lap);
-      const float4 pm = ld4s(stage + S::OFF_PREV + k * PPLANE + ly * TX3 + lx);
-      const float4 cv = ld4s(stage + S::OFF_CC + ly * TX3 + lx);
-      const float gzy = gz[z] + gyv;
       float nv[4];
-#pragma unroll
-      for (int j = 0; j < 4; j += 2) {  // cc * lap + (p + b (p - pm)), in pairs
-        const float2 bb = f2(sponge_b(gzy + gxv[j]), sponge_b(gzy + gxv[j + 1]));
-        const float2 p = half2of(Q[C % NQ], j);
-        const float2 d = __ffma2_rn(half2of(pm, j), f2(-1.f, -1.f), p);
-        const float2 n2 = __ffma2_rn(half2of(cv, j), f2(lap[j], lap[j + 1]), __ffma2_rn(bb, d, p));
-        nv[j] = n2.x;
-        nv[j + 1] = n2.y;
-      }
-      // injection / sampling at this level: staged in this warp's two rows of
-      // the p^{n-1} plane (already consumed); entry .x is the point's index
-      // in that plane, and its row / 2 names the warp that owns it
-      if (inj_z == z || smp_z == z) {
-        float* pl = stage + S::OFF_PREV + k * PPLANE;
-        const int wrow = ly >> 1;
-        __syncwarp();
-        *reinterpret_cast<float4*>(pl + ly * TX3 + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
-        __syncwarp();
-        int e_end = ie_cur;
-        while (e_end < ie_end && P.inj[e_end].w == z) e_end++;
-        for (int e = ie_cur + lane; e < e_end; e += 32) {
-          const int4 en = P.inj[e];
-          if ((en.x / TX3) >> 1 != wrow) continue;
-          const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + en.x / TX3, x0 + en.x % TX3));
-          pl[en.x] += ccp * (__int_as_float(en.z) *
-                             P.series[(long long)b * P.series_bstride + (long long)P.t * P.series_ld + en.y]);
-        }
-        ie_cur = e_end;
-        inj_z = ie_cur < ie_end ? P.inj[ie_cur].w : 0x7fffffff;
-        __syncwarp();
-        const float4 v = ld4s(pl + ly * TX3 + lx);
-        nv[0] = v.x; nv[1] = v.y; nv[2] = v.z; nv[3] = v.w;
-        int s_end = se_cur;
-        while (s_end < se_end && P.smp4[s_end].z == z) s_end++;
-        for (int e = se_cur + lane; e < s_end; e += 32) {
-          const int4 en = P.smp4[e];
-          if ((en.x / TX3) >> 1 != wrow) continue;
-          P.smp_out[(long long)b * P.smp_bstride_out + (long long)P.t * P.smp_ld + en.y] = pl[en.x];
-        }
-        se_cur = s_end;
-        smp_z = se_cur < se_end ? P.smp4[se_cur].z : 0x7fffffff;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
+      advance<C>(z, hpl, stage, nv);
+      inject(z, stage, nv);
       if (ADJ) {
         float lps[4];
         lap3<C, ISO, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
@@ -364,15 +465,7 @@ struct March3D {
           store_g(z, make_float4(g01.x, g01.y, g23.x, g23.y));
         }
       }
-      if (colv) {
-        float* o = P.pool + (long long)P.s_out * P.slot_elems + (long long)b * L.field + L.off(z, gy, gx);
-        if (gx + 3 < L.nxp) {
-          *reinterpret_cast<float4*>(o) = make_float4(nv[0], nv[1], nv[2], nv[3]);
-        } else {
-          for (int j = 0; j < 4; j++)
-            if (gx + j < L.nxp) o[j] = nv[j];
-        }
-      }
+      store_p(z, nv);
     }
     if (z >= 0) zc++;
     // release the slot of sequence q-4: its halo plane served level q-8 above
@@ -385,6 +478,7 @@ struct March3D {
     if (++hslot == NST) hslot = 0;
     return true;
   }
+
 };
 
 template <bool ADJ, bool ISO, int NQ, bool PAIR>
@@ -401,6 +495,8 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   uint64_t* xfull = empty + S::NST;
   uint64_t* xempty = xfull + S::NXB / 2;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S::NST + S::NXB);
+  int* deps_ok = const_cast<int*>(abort_flag) + 1;  // multi-step: columns whose neighbourhood is ready
+  int* wdone = deps_ok + 1;                          // multi-step: consumer warps done with column ic
 
   const int tid = threadIdx.x, warp = tid >> 5;
   March3D<ADJ, ISO, NQ, PAIR> M{L, K, P, &tm_halo, &tm_plain, &tm_cc, &tm_g, sm, full, empty, xfull, xempty,
@@ -416,8 +512,23 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   // c runs columns c, c + gridDim.x, ... back to back (a persistent grid of
   // one CTA per SM), so the TMA ring runs on from one column into the next
   // instead of draining and refilling at every column.
+  //
+  // A multi-step launch (P.steps set; persistent grids only, launched
+  // cooperatively) runs P.nsteps time steps this way, chained column by
+  // column instead of by kernel boundaries: the loads of column (step n,
+  // unit u, tile) wait until the 3 x 3 tile neighbourhood of u has finished
+  // step n - 1 (progress flags P.done[u][tile], zero at launch).  A level's
+  // slot is next written one or two steps after it was read as the stepped
+  // level, so the same condition covers the write-after-read hazards of the
+  // slots.  Roles in the producer warpgroup: warp 8 lane 0 the TMA ring,
+  // warp 9 lane 0 polls the flags of upcoming columns, warp 10 lane 0
+  // publishes a column's flag once every consumer warp has stored it.
   const int nunits = P.nunits3;
   const int ncols = P.ntiles * nunits;
+  const bool multi = P.steps != nullptr;
+  const int nsteps = multi ? P.nsteps : 1;
+  const int G = (int)gridDim.x;
+  const int my_cols = (int)blockIdx.x < ncols ? (ncols - 1 - (int)blockIdx.x) / G + 1 : 0;
   M.lx = 4 * (M.lane & 15);
   M.last_q = L.nzp + 7;
   M.gz = gz;
@@ -442,6 +553,8 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     }
     for (int i = 0; i < S::NXB; i++) mbar_init(&xfull[i], 1);  // xfull and xempty: one arrival each
     *abort_flag = 0;
+    *deps_ok = my_cols;  // step 0 depends on nothing in the launch
+    for (int i = 0; i < WDONE3; i++) wdone[i] = 0;
     fence_mbar_init();
   }
   for (int i = tid; i < L.nzp; i += NTHREADS3) gz[i] = P.gtab[i];
@@ -453,17 +566,27 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
       // sequence g (counted over all columns) into slot g % NST once every
       // consumer warp has released sequence g - NST (whose halo plane served
       // the level 4 below it, or, at a column's end, landed last)
-      int gq = 0;
+      int gq = 0, ic = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < ncols && ok; it += gridDim.x) {
-        M.set_column(it, nunits);
-        for (M.pq = 0; M.pq <= M.last_q; gq++) {
-          if (gq >= S::NST &&
-              !mbar_wait_abortable(&empty[M.pst], (uint32_t)((gq / S::NST - 1) & 1), P.status, abort_flag)) {
-            ok = false;
-            break;
+      for (int n = 0; n < nsteps && ok; n++) {
+        M.set_step(n);
+        for (int it = blockIdx.x; it < ncols && ok; it += G, ic++) {
+          M.set_column(it, nunits);
+          if (n > 0) {  // the column's neighbourhood has finished step n - 1 (counted by warp 9)
+            if (!wait_counter(deps_ok, ic, P.status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            fence_proxy_async_global();
           }
-          M.issue();
+          for (M.pq = 0; M.pq <= M.last_q; gq++) {
+            if (gq >= S::NST &&
+                !mbar_wait_abortable(&empty[M.pst], (uint32_t)((gq / S::NST - 1) & 1), P.status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            M.issue();
+          }
         }
       }
       if (!ok) {  // gave up: bounded wait for the copies in flight
@@ -472,6 +595,29 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
           while (!mbar_try_wait(&full[i % S::NST], (uint32_t)((i / S::NST) & 1)) && clock64() - t0 < (1LL << 24)) {
           }
         }
+      }
+    } else if (multi && warp == NCW3 + 1 && M.lane == 0) {
+      // columns of steps 1.. in the producer's order: neighbourhood ready
+      for (int n = 1, ic = my_cols; n < nsteps; n++)
+        for (int kk = 0; kk < my_cols; kk++, ic++) {
+          int u, tile;
+          column_of(P, (int)blockIdx.x + kk * G, nunits, u, tile);
+          if (!wait_columns3(P.done, P.ntx, P.ntiles, P.status, u, tile, n, abort_flag)) return;
+          asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(deps_ok)), "r"(ic + 1) : "memory");
+        }
+    } else if (multi && warp == NCW3 + 2 && M.lane == 0) {
+      // column ic of this CTA (step ic / my_cols) is complete when every
+      // consumer warp has counted it in wdone[ic % WDONE3]; its flag (steps
+      // done) is then published at GPU scope.  The last step's flags are
+      // read by nobody.
+      const int nic = my_cols * (nsteps - 1);
+      for (int ic = 0; ic < nic; ic++) {
+        const int n = ic / my_cols, kk = ic - n * my_cols;
+        if (!wait_counter(&wdone[ic % WDONE3], NCW3 * (ic / WDONE3 + 1) - 1, P.status, abort_flag)) return;
+        fence_acq_rel_gpu();
+        int u, tile;
+        column_of(P, (int)blockIdx.x + kk * G, nunits, u, tile);
+        st_relaxed_gpu(P.done + (long long)u * P.ntiles + tile, n + 1);
       }
     }
     return;
@@ -491,7 +637,10 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   if (!M.template land<(k) + 1>()) return;                  \
   if (!M.template level<((k) + 6) % 10>(q + (k))) return;   \
   if (!M.template level<((k) + 7) % 10>(q + (k) + 1)) return;
-  for (int it = blockIdx.x; it < ncols; it += gridDim.x) {
+  int icc = 0;
+  for (int n = 0; n < nsteps; n++) {
+  M.set_step(n);
+  for (int it = blockIdx.x; it < ncols; it += G, icc++) {
     M.set_column(it, nunits);
     M.gyv = M.gy < L.nyp ? __ldg(P.gtab + L.nzp + M.gy) : 0.f;
 #pragma unroll
@@ -535,6 +684,11 @@ step3d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     // pair tiles: the first wavefield's warps still hold the column's last level
     if (ADJ && PAIR && M.k == 0 && !M.pair_finish(L.nzp - 1, M.zc - 1)) return;
     M.carry = true;
+    if (multi) {  // this warp's stores of the column are done: count it for the publisher
+      __syncwarp();
+      if (M.lane == 0) red_release_cta_shared(&wdone[icc % WDONE3], 1);
+    }
+  }
   }
 #undef FWI_ONE
 #undef FWI_TWO
@@ -548,8 +702,23 @@ static cudaError_t launch3(const CUtensorMap& tm_halo, const CUtensorMap& tm_pla
   auto kern = P.zpair3 ? step3d_kernel<ADJ, ISO, 10, PAIR> : step3d_kernel<ADJ, ISO, 9, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  kern<<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
-  return cudaGetLastError();
+  if (!P.steps) {
+    kern<<<grid, NTHREADS3, bytes, st>>>(tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
+    return cudaGetLastError();
+  }
+  // multi-step: CTAs wait on one another's progress flags, so all of them
+  // must be resident at once (a cooperative launch refuses a grid that is not)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NTHREADS3);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, tm_halo, tm_plain, tm_cc, tm_g, L, K, P);
 }
 
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain, const CUtensorMap& tm_cc,
@@ -558,6 +727,8 @@ cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMa
   // columns: tiles x units (one wavefield, or a pair of supergathers of one
   // sample), dealt in turn to a persistent grid of at most one CTA per SM
   if (P.pair3 && (B % 2 || P.nsg % 2)) return cudaErrorInvalidValue;
+  // a multi-step launch needs the persistent grid, its step table and flags
+  if (P.steps && (P.ctas_per_sm3 != 1 || P.nsteps < 1 || !P.done)) return cudaErrorInvalidValue;
   StepParams Q = P;
   Q.nunits3 = P.pair3 ? B / 2 : B;
   const long long ncols = (long long)P.ntiles * Q.nunits3;

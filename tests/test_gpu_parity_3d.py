@@ -171,8 +171,9 @@ def test_3d_step_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    # adjoint on 64 x 16 tiles; bit 3: persistent grid
+    # adjoint on 64 x 16 tiles; bit 3: persistent grid; bit 4 (with bit 3): one multi-step launch per phase
     for var in ((0, 0), (1, 1), (2, 3), (3, 2), (4, 0), (7, 1), (5, 2), (6, 3), (11, 9), (12, 10), (15, 11),
+                (25, 27), (30, 24),
                 (8, 8)):
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
@@ -183,6 +184,51 @@ def test_3d_step_variants_bit_identical(P):
         assert (got["forward"], got["adjoint"]) == var
         assert ("pairs" in got["forward_name"]) == bool(var[0] & 4)
         assert ("persistent" in got["forward_name"]) == bool(var[0] & 8)
+        assert ("multi-step" in got["forward_name"]) == bool(var[0] & 16)
+        ctx.close()
+    torch.cuda.synchronize()
+    for m, g, rec in out[1:]:
+        assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0]) and torch.equal(rec, out[0][2])
+
+
+def wide3d(nt=60, ns=4):
+    # a wide, shallow grid: 36 x 140 x 270 padded points, 5 x 9 = 45 tiles of
+    # 64 x 16 per wavefield
+    nz, ny, nx, h = 16, 120, 250, 20.0
+    src = np.array([[1, 20 + 25 * i, 30 + 55 * i] for i in range(ns)], np.int32)
+    rec = np.array([[2, y, x] for y in range(3, ny, 9) for x in range(2, nx, 11)], np.int32)
+    return Workload("wide3d", 3, nz, ny, nx, h, h, h, 10, 2e-3, nt, 8.0, 1500.0, 3500.0, src, rec, [ns], 1, 11)
+
+
+def test_3d_multistep_launch_many_columns_bit_identical(P):
+    # 2 samples x 4 supergathers of one shot on the wide grid: 45 tiles x 4
+    # wavefields = 180 columns per sample, more than one per SM in every
+    # launch however the samples are chunked, so a CTA of a multi-step launch
+    # runs several columns per step and waits on other CTAs' columns through
+    # the progress flags; records and gradients must equal those of the
+    # one-launch-per-step variants bit for bit (sources, receivers and
+    # checkpoint segments)
+    import torch
+    w = wide3d()
+    nsamp, sg = 2, [1, 1, 1, 1]
+    tiles = -(-(w.nx + 2 * w.nb) // 64) * -(-(w.ny + 2 * w.nb) // 16)
+    assert tiles * len(sg) > 152
+    v = torch.tensor(np.stack([synth.models.random_smooth_model(w.shape, 90 + s, 1500, 3000)
+                               for s in range(nsamp)])).cuda()
+    d_obs = torch.tensor(synth.random_records(w, 13)).cuda()
+    encs = [P.encode(10, s, w.ns) for s in range(nsamp)]
+    perm = np.stack([e[0] for e in encs])
+    wt = np.stack([e[1] for e in encs])
+    out = []
+    for var in ((1, 0), (25, 24), (27, 25), (24, 9)):
+        ctx = P.FWI(w.grid_dict(), w.src, w.rec, len(sg) * nsamp, 1 << 30)
+        ctx.set_variants(*var)
+        m, g = ctx.gradient(v, perm, wt, sg, d_obs, 1.0)
+        rec = ctx.forward(v, perm, wt, sg)
+        out.append((m, g, rec))
+        got = ctx.variants()
+        assert ("multi-step" in got["forward_name"]) == bool(var[0] & 16)
+        assert ("multi-step" in got["adjoint_name"]) == bool(var[1] & 16)
         ctx.close()
     torch.cuda.synchronize()
     for m, g, rec in out[1:]:
@@ -202,15 +248,15 @@ def test_3d_pair_tile_adjoint_variants_bit_identical(P):
     perm = np.stack([e[0] for e in encs])
     wt = np.stack([e[1] for e in encs])
     out = []
-    for var in ((3, 4), (0, 5), (1, 6), (2, 7), (11, 12), (3, 13), (3, 0)):
+    for var in ((3, 4), (0, 5), (1, 6), (2, 7), (11, 12), (3, 13), (27, 28), (3, 0)):
         ctx = P.FWI(w.grid_dict(), w.src, w.rec, 4, 1 << 31)
         ctx.set_variants(*var)
         out.append(ctx.gradient(v, perm, wt, [2, 2], d_obs, 1.0))
         assert ("pairs" in ctx.variants()["adjoint_name"]) == bool(var[1] & 4)
         ctx.close()
     torch.cuda.synchronize()
-    for m, g in out[1:6]:
+    for m, g in out[1:7]:
         assert torch.equal(g, out[0][1]) and torch.equal(m, out[0][0])
-    m0, g0 = out[6]
+    m0, g0 = out[7]
     assert torch.equal(m0, out[0][0])
     assert float((g0 - out[0][1]).norm() / g0.norm()) < 1e-6
