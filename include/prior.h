@@ -115,6 +115,26 @@ int prior_upcat_bf16(const void* Lo, int C1, const void* Skip, int C2, int nimg,
 int prior_output(const float* D, int ldd, const float* x, int nimg, int H, int W, int Hp, int Wp, float scale,
                  float bo, float* out, void* stream);
 
+// The same four layers over volumes, for the 3D network (NDHWC, [nimg][D][H][W][C]):
+//   prior_first_conv3d_bf16: x [nimg][D][H][W] FP32 edge-replicated to [Dp][Hp][Wp];
+//     the 3x3x3 convolution of prior_conv3x3x3_bf16 (tap = dz*9 + dy*3 + dx) over
+//     the 2-channel input, Wt [Cout][27][2] BF16, 54 products per output;
+//     Y [nimg][Dp][Hp][Wp][Cout] BF16; 8 <= Cout <= 128, Cout % 8 == 0.
+//   prior_pool2_3d_bf16: 2 x 2 x 2 average (FP32 sum / 8, one rounding); D, H, W even.
+//   prior_upcat3d_bf16: Y[n][d][h][w][c] = Lo[n][d/2][h/2][w/2][c] for c < C1,
+//     Skip[n][d][h][w][c - C1] otherwise; D, H, W even.
+//   prior_output3d: out[n][d][h][w] = scale * x[n][d][h][w] + D[(((n*Dp + d)*Hp + h)*Wp + w) * ldd] + bo.
+// Errors as above: PRIOR_ERR_ARG for a null or unaligned pointer or a size out
+// of range (nothing launched), PRIOR_ERR_CUDA if the launch fails.
+int prior_first_conv3d_bf16(const float* x, int nimg, int D, int H, int W, int Dp, int Hp, int Wp, float scale,
+                            const float* sigma, const void* Wt, const float* bias, int Cout, int relu, void* Y,
+                            void* stream);
+int prior_pool2_3d_bf16(const void* X, int nimg, int D, int H, int W, int C, void* Y, void* stream);
+int prior_upcat3d_bf16(const void* Lo, int C1, const void* Skip, int C2, int nimg, int D, int H, int W, void* Y,
+                       void* stream);
+int prior_output3d(const float* Dm, int ldd, const float* x, int nimg, int D, int H, int W, int Dp, int Hp, int Wp,
+                   float scale, float bo, float* out, void* stream);
+
 // Reads and clears the internal status word (synchronises the stream).
 int prior_last_status(void* stream);
 

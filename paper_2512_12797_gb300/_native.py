@@ -21,7 +21,8 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_encode", "fwi_forward", "fwi_gradie
 # every symbol prior.h declares
 PRIOR_EXPORTS = ["prior_gemm_bf16", "prior_conv3x3_bf16", "prior_conv3x3_wgrad_bf16", "prior_conv3x3x3_bf16",
                  "prior_conv3x3x3_wgrad_bf16", "prior_last_status", "prior_first_conv_bf16", "prior_pool2_bf16",
-                 "prior_upcat_bf16", "prior_output"]
+                 "prior_upcat_bf16", "prior_output", "prior_first_conv3d_bf16", "prior_pool2_3d_bf16",
+                 "prior_upcat3d_bf16", "prior_output3d"]
 
 
 class FwiGrid(ctypes.Structure):
@@ -105,6 +106,12 @@ _SIGS = {
                                         ctypes.c_int, _P, _P]),
     "prior_output": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P]),
+    "prior_first_conv3d_bf16": (ctypes.c_int, [_P] + [ctypes.c_int] * 7 + [ctypes.c_float, _P, _P, _P, ctypes.c_int,
+                                                                          ctypes.c_int, _P, _P]),
+    "prior_pool2_3d_bf16": (ctypes.c_int, [_P] + [ctypes.c_int] * 5 + [_P, _P]),
+    "prior_upcat3d_bf16": (ctypes.c_int, [_P, ctypes.c_int, _P] + [ctypes.c_int] * 5 + [_P, _P]),
+    "prior_output3d": (ctypes.c_int, [_P, ctypes.c_int, _P] + [ctypes.c_int] * 7 + [ctypes.c_float, ctypes.c_float,
+                                                                                    _P, _P]),
 }
 
 

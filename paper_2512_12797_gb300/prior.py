@@ -91,6 +91,49 @@ def output(D, x, Hp, Wp, scale, bo):
     return out
 
 
+def first_conv3d(x, D, H, W, Dp, Hp, Wp, scale, sigma, Wt2, bias, relu=True):
+    """First layer of the 3D network: the 2-channel input (scale * x [n, D, H, W]
+    edge-padded to Dp x Hp x Wp, and sigma per volume), 3x3x3 convolution with
+    Wt2 [Cout][27][2] BF16 (prior_first_conv3d_bf16); returns [n, Dp, Hp, Wp, Cout] BF16."""
+    n = x.shape[0]
+    Cout = Wt2.shape[0]
+    out = torch.empty((n, Dp, Hp, Wp, Cout), dtype=torch.bfloat16, device=x.device)
+    rc = _native.lib().prior_first_conv3d_bf16(x.data_ptr(), n, D, H, W, Dp, Hp, Wp, float(scale), sigma.data_ptr(),
+                                               Wt2.data_ptr(), bias.data_ptr() if bias is not None else None, Cout,
+                                               int(relu), out.data_ptr(), _stream())
+    _check(rc, "prior_first_conv3d_bf16")
+    return out
+
+
+def pool2_3d(X):
+    """2 x 2 x 2 average pooling of X [n, D, H, W, C] BF16 (prior_pool2_3d_bf16)."""
+    n, D, H, W, C = X.shape
+    out = torch.empty((n, D // 2, H // 2, W // 2, C), dtype=torch.bfloat16, device=X.device)
+    _check(_native.lib().prior_pool2_3d_bf16(X.data_ptr(), n, D, H, W, C, out.data_ptr(), _stream()),
+           "prior_pool2_3d_bf16")
+    return out
+
+
+def upcat3d(lo, skip):
+    """[up2(lo), skip] along channels: lo [n, D/2, H/2, W/2, C1], skip [n, D, H, W, C2] (prior_upcat3d_bf16)."""
+    n, D, H, W, C2 = skip.shape
+    C1 = lo.shape[-1]
+    out = torch.empty((n, D, H, W, C1 + C2), dtype=torch.bfloat16, device=skip.device)
+    _check(_native.lib().prior_upcat3d_bf16(lo.data_ptr(), C1, skip.data_ptr(), C2, n, D, H, W, out.data_ptr(),
+                                            _stream()), "prior_upcat3d_bf16")
+    return out
+
+
+def output3d(Dm, x, Dp, Hp, Wp, scale, bo):
+    """x0-hat = scale * x + Dm[:, 0] + bo on the physical part [n, D, H, W] of the
+    padded volume (prior_output3d); Dm [n*Dp*Hp*Wp, ldd] FP32."""
+    n, D, H, W = x.shape
+    out = torch.empty_like(x)
+    _check(_native.lib().prior_output3d(Dm.data_ptr(), Dm.stride(0), x.data_ptr(), n, D, H, W, Dp, Hp, Wp,
+                                        float(scale), float(bo), out.data_ptr(), _stream()), "prior_output3d")
+    return out
+
+
 def last_status():
     """Device status word of the prior kernels (read and cleared)."""
     return _native.lib().prior_last_status(_stream())

@@ -9,7 +9,11 @@ forward_torch  -- plain PyTorch FP32 (training with autograd, reference);
 forward_tc     -- every 3x3x3 convolution on prior.conv3x3x3 (tcgen05, BF16
                   activations, FP32 accumulation), the 1x1x1 output on
                   prior.gemm_bf16; pooling, upsampling, concatenation are
-                  tensor reshapes;
+                  tensor reshapes (the training path, which keeps each
+                  layer's input for the backward);
+_forward_tc    -- the inference path of UNet3DDenoiser: the same network with
+                  the input build, padding, pooling, upsample-and-join and
+                  output on the layout kernels of prior.py;
 backward_tc    -- data and weight gradients of every 3x3x3 convolution on the
                   tcgen05 kernels (gradients FP32 between layers).
 """
@@ -71,6 +75,7 @@ def pack(p):
     wo = torch.zeros(32, 64, device=p["out.w"].device)
     wo[0] = p["out.w"].detach().float().view(64)
     q["out"] = (wo.to(torch.bfloat16).contiguous(), float(p["out.b"].detach().float().item()))
+    q["e1a2"] = (q["e1a"][0][:, :, :2].contiguous(), q["e1a"][1])  # first layer's 2 real input channels
     return q
 
 
@@ -129,6 +134,34 @@ def forward_tc_train(q, y, sigma):
 
 def forward_tc(q, y, sigma):
     return forward_tc_train(q, y, sigma)[0]
+
+
+def _forward_tc(q, x, D, H, W, Dp, Hp, Wp, scale, sigma):
+    """x0-hat of y = scale * x [n, D, H, W], evaluated on the volume
+    edge-padded to Dp x Hp x Wp and cropped back, with no PyTorch reshapes
+    between the kernels: the first layer builds its 2-channel input on the fly
+    (prior_first_conv3d_bf16), the 3x3x3 layers run on tcgen05, pooling and
+    the decoder's upsample-and-join are single passes (prior_pool2_3d_bf16,
+    prior_upcat3d_bf16), and the 1x1x1 output is a tcgen05 GEMM whose result
+    prior_output3d adds to y on the physical volume."""
+    def c(h, name):
+        w, b = q[name]
+        return TC.conv3x3x3(h, w, bias=b, relu=True)
+
+    w2, b2 = q["e1a2"]
+    h = TC.first_conv3d(x.contiguous(), D, H, W, Dp, Hp, Wp, scale, sigma.float().contiguous(), w2, b2, relu=True)
+    e1 = c(h, "e1b")
+    h = c(TC.pool2_3d(e1), "e2a")
+    e2 = c(h, "e2b")
+    h = c(TC.pool2_3d(e2), "ba")
+    h = c(h, "bb")
+    h = c(TC.upcat3d(h, e2), "d2a")
+    h = c(h, "d2b")
+    h = c(TC.upcat3d(h, e1), "d1a")
+    h = c(h, "d1b")
+    wo, bo = q["out"]
+    Dm = TC.gemm_bf16(h.view(-1, 64), wo)
+    return TC.output3d(Dm, x.contiguous(), Dp, Hp, Wp, scale, bo)
 
 
 def backward_tc(q, saved, g):
@@ -260,8 +293,6 @@ class UNet3DDenoiser:
 
     def __call__(self, x_t, abar_t):
         n, D, H, W = x_t.shape
-        y = x_t / math.sqrt(abar_t)
         sig = torch.full((n,), math.sqrt((1.0 - abar_t) / abar_t), device=x_t.device)
         Dp, Hp, Wp = tile_shape(D, H, W)
-        yp = F.pad(y[:, None], (0, Wp - W, 0, Hp - H, 0, Dp - D), mode="replicate")[:, 0].contiguous()
-        return forward_tc(self.q, yp, sig)[:, :D, :H, :W].contiguous()
+        return _forward_tc(self.q, x_t, D, H, W, Dp, Hp, Wp, 1.0 / math.sqrt(abar_t), sig)

@@ -192,3 +192,47 @@ def test_pool_and_upcat_layout_kernels(P):
     up = P.upcat(lo.cuda(), X.cuda()).cpu()
     assert torch.equal(up[..., :C1], lo.repeat_interleave(2, 1).repeat_interleave(2, 2))
     assert torch.equal(up[..., C1:], X)
+
+
+@pytest.mark.parametrize("n,D,H,W,Dp,Hp,Wp,Cout", [(2, 6, 10, 14, 8, 16, 16, 64), (1, 8, 8, 8, 8, 8, 8, 32)])
+def test_first_conv3d_matches_oracle(P, n, D, H, W, Dp, Hp, Wp, Cout):
+    # the 3D network's input built on the fly (scaled volume, edge-padded to
+    # Dp x Hp x Wp, noise-level channel; both rounded to BF16) and convolved
+    # 3x3x3 from 2 channels
+    import torch
+    g = torch.Generator().manual_seed(n * 100 + D)
+    x = torch.randn((n, D, H, W), generator=g) * 0.7
+    sig = torch.tensor([0.3, 1.7][:n])
+    Wt = _bf16(torch, (Cout, 27, 2), 7 + Cout)
+    bias = torch.randn(Cout, generator=g) * 0.1
+    scale = 0.8
+    Y = P.first_conv3d(x.cuda(), D, H, W, Dp, Hp, Wp, scale, sig.cuda(), Wt.cuda(), bias.cuda(), relu=True)
+    xin = np.zeros((n, Dp, Hp, Wp, 2))
+    xp = np.pad((scale * x).numpy(), ((0, 0), (0, Dp - D), (0, Hp - H), (0, Wp - W)), mode="edge")
+    xin[..., 0] = torch.tensor(xp).float().to(torch.bfloat16).double().numpy()
+    xin[..., 1] = sig.to(torch.bfloat16).double().numpy()[:, None, None, None]
+    ref = np.maximum(PO.conv3x3x3(xin, Wt.float().numpy()) + bias.double().numpy(), 0.0)
+    got = Y.cpu().double().numpy()
+    assert _rel(got, ref) < 4e-3
+    assert np.max(np.abs(got - ref)) <= 2 ** -7 * np.max(np.abs(ref))
+
+
+def test_pool_upcat_output_3d_layout_kernels(P):
+    import torch
+    n, D, H, W, C1, C2 = 2, 4, 8, 16, 64, 32
+    X = _bf16(torch, (n, D, H, W, C2), 19)
+    pooled = P.pool2_3d(X.cuda()).cpu()
+    ref = X.double().numpy().reshape(n, D // 2, 2, H // 2, 2, W // 2, 2, C2).mean(axis=(2, 4, 6))
+    assert np.max(np.abs(pooled.double().numpy() - ref)) <= 2 ** -8 * np.max(np.abs(ref))
+    lo = _bf16(torch, (n, D // 2, H // 2, W // 2, C1), 20)
+    up = P.upcat3d(lo.cuda(), X.cuda()).cpu()
+    assert torch.equal(up[..., :C1], lo.repeat_interleave(2, 1).repeat_interleave(2, 2).repeat_interleave(2, 3))
+    assert torch.equal(up[..., C1:], X)
+    # output on the physical part of a padded volume, D a column of rows of 32 floats
+    Dp, Hp, Wp = D + 2, H + 3, W + 4
+    g = torch.Generator().manual_seed(21)
+    x = torch.randn((n, D, H, W), generator=g)
+    Dm = torch.randn((n * Dp * Hp * Wp, 32), generator=g)
+    out = P.output3d(Dm.cuda(), x.cuda(), Dp, Hp, Wp, 1.5, 0.25).cpu()
+    ref = 1.5 * x + Dm[:, 0].view(n, Dp, Hp, Wp)[:, :D, :H, :W] + 0.25
+    assert torch.allclose(out, ref, rtol=1e-6, atol=1e-6)

@@ -57,6 +57,28 @@ def test_tc3_forward_matches_bf16_reference(U3):
     assert r32 < 0.1, r32
 
 
+def test_denoiser_layout_kernels_match_reshape_path(U3):
+    # UNet3DDenoiser runs the network on the layout kernels (input built and
+    # padded in the first layer, pooling, upsample-and-join, output); the
+    # training path builds the same tensors with PyTorch reshapes.  Same
+    # BF16 activations up to the first layer's FP32 summation order.
+    import math
+    import torch
+    import torch.nn.functional as F
+    p, gen = _params(torch, U3, 4)
+    x_t = torch.tensor(SP.volume_patches(2, 32, 6)).cuda()[:, 3:29, 2:30, 1:31].contiguous()  # 26 x 28 x 30
+    abar = 0.6
+    got = U3.UNet3DDenoiser(p)(x_t, abar)
+    n, D, H, W = x_t.shape
+    Dp, Hp, Wp = U3.tile_shape(D, H, W)
+    y = x_t / math.sqrt(abar)
+    yp = F.pad(y[:, None], (0, Wp - W, 0, Hp - H, 0, Dp - D), mode="replicate")[:, 0].contiguous()
+    sig = torch.full((n,), math.sqrt((1.0 - abar) / abar), device=x_t.device)
+    ref = U3.forward_tc(U3.pack(p), yp, sig)[:, :D, :H, :W]
+    r = float((got - ref).norm() / (ref - y).norm())
+    assert got.shape == x_t.shape and r < 1e-2, r
+
+
 def test_tc3_backward_matches_autograd(U3):
     import torch
     p, gen = _params(torch, U3, 5)
