@@ -548,6 +548,8 @@ def native_arm(args):
                       "checkpoint_plan": r["plan"],
                       "step_kernels": {"forward": r["variants"]["forward_name"],
                                        "adjoint": r["variants"]["adjoint_name"],
+                                       "forward_index": r["variants"]["forward"],
+                                       "adjoint_index": r["variants"]["adjoint"],
                                        "tuner_ms_forward": r["variants"]["forward_ms"],
                                        "tuner_ms_adjoint": r["variants"]["adjoint_ms"]}},
            "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "roofline": r["roofline"],

@@ -261,6 +261,8 @@ Coef make_coef(const fwi_grid* g) {
   K.gdt = (float)(gmax * g->dt);
   K.inv_nb = g->nb > 0 ? (float)(1.0 / g->nb) : 0.f;
   K.c0_2d = (float)(A8[0] / (g->hx * g->hx) + A8[0] / (g->hz * g->hz));
+  K.c0_3d = g->ndim == 3 ? (float)(A8[0] / (g->hx * g->hx) + A8[0] / (g->hy * g->hy) + A8[0] / (g->hz * g->hz))
+                         : 0.f;
   return K;
 }
 

@@ -44,6 +44,7 @@ struct Coef {
   float gdt;                  // gmax * dt
   float inv_nb;               // 1 / nb (0 when nb == 0)
   float c0_2d;                // a_0/hx^2 + a_0/hz^2: centre weight of the 2D Laplacian in plain form
+  float c0_3d;                // a_0/hx^2 + a_0/hy^2 + a_0/hz^2: the same for the 3D Laplacian
 };
 
 // Slots and record time of one step of a multi-step launch.

@@ -206,6 +206,45 @@ __device__ __forceinline__ bool wait_counter(const int* c, int v, int* status, v
   return true;
 }
 
+// The Laplacian of the snapshot for the imaging condition, in the plain form
+// c0 p + sum_a sum_k c_{a,k} (p_{+k} + p_{-k}): it enters the gradient, not
+// the recursion, so it needs neither the bracket form's exact zero on a
+// constant field nor its 2p subtractions (the 2D adjoint does the same).
+// Operand loads as lap3.
+template <int C, int NQ>
+__device__ __forceinline__ void lap3_img(const float* __restrict__ H, const float4 (&Q)[NQ], int ly, int lx,
+                                         const Coef& K, float (&lap)[4]) {
+  const float* row = H + (ly + HALO) * HX3;
+  const float4 xl = ld4s(row + lx), xr = ld4s(row + lx + 8);
+  const float4 ce = Q[C % NQ];
+  const float w[12] = {xl.x, xl.y, xl.z, xl.w, ce.x, ce.y, ce.z, ce.w, xr.x, xr.y, xr.z, xr.w};
+  float4 yn[8];
+#pragma unroll
+  for (int k = 1; k <= 4; k++) {
+    yn[k - 1] = ld4s(H + (ly + HALO - k) * HX3 + lx + 4);
+    yn[k + 3] = ld4s(H + (ly + HALO + k) * HX3 + lx + 4);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; j += 2) {
+    const float2 p = f2(w[4 + j], w[5 + j]);
+    auto xs = [&](int k) {
+      return (k & 1) ? f2(w[4 + j + k] + w[4 + j - k], w[5 + j + k] + w[5 + j - k])
+                     : __fadd2_rn(f2(w[4 + j + k], w[5 + j + k]), f2(w[4 + j - k], w[5 + j - k]));
+    };
+    auto ys = [&](int k) { return __fadd2_rn(half2of(yn[k + 3], j), half2of(yn[k - 1], j)); };
+    auto zs = [&](int k) { return __fadd2_rn(half2of(Q[(C + k) % NQ], j), half2of(Q[(C + NQ - k) % NQ], j)); };
+    float2 a = __fmul2_rn(f2(K.c0_3d, K.c0_3d), p);
+#pragma unroll
+    for (int k = 4; k >= 1; k--) {
+      a = __ffma2_rn(f2(K.cx[k], K.cx[k]), xs(k), a);
+      a = __ffma2_rn(f2(K.cy[k], K.cy[k]), ys(k), a);
+      a = __ffma2_rn(f2(K.cz[k], K.cz[k]), zs(k), a);
+    }
+    lap[j] = a.x;
+    lap[j + 1] = a.y;
+  }
+}
+
 template <bool ADJ, bool ISO, int NQ, bool PAIR>
 struct March3D {
   using S = Smem3D<ADJ, PAIR>;
@@ -432,7 +471,7 @@ struct March3D {
       inject(z, stage, nv);
       if (ADJ) {
         float lps[4];
-        lap3<C, ISO, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
+        lap3_img<C, NQ>(hpl + S::OFF_SNAP, QS, ly, lx, K, lps);
         float4 g = ld4s(stage + S::OFF_G + ly * TX3 + lx);
         if (PAIR) {
           // The second wavefield's warp hands q L p of level z to the first's
