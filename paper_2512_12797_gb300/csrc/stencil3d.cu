@@ -419,29 +419,41 @@ struct March3D {
     __syncwarp();
     *reinterpret_cast<float4*>(pl + ly * TX3 + lx) = make_float4(nv[0], nv[1], nv[2], nv[3]);
     __syncwarp();
-    int e_end = ie_cur;
-    while (e_end < ie_end && P.inj[e_end].w == z) e_end++;
-    for (int e = ie_cur + lane; e < e_end; e += 32) {
-      const int4 en = P.inj[e];
-      if ((en.x / TX3) >> 1 != wrow) continue;
-      const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + en.x / TX3, x0 + en.x % TX3));
-      pl[en.x] += ccp * (__int_as_float(en.z) *
-                         P.series[(long long)b * P.series_bstride + (long long)t * P.series_ld + en.y]);
+    // The entries of level z are the next ones under each cursor (lists are
+    // sorted by z); the warp reads them 32 at a time, and a ballot counts
+    // those at level z (a prefix of the 32).  Lane n of the last read holds
+    // the next entry, whose level becomes the cursor's.
+    while (inj_z == z) {
+      const int e = ie_cur + lane;
+      int4 en = make_int4(0, 0, 0, 0x7fffffff);
+      if (e < ie_end) en = P.inj[e];
+      const bool here = en.w == z;
+      const int n = __popc(__ballot_sync(0xffffffffu, here));
+      // Entries of one list never share a point (fwi_create rejects duplicate
+      // receivers, and each wavefield's coincident sources are merged into
+      // one entry), so the lanes add to distinct words.
+      if (here && (en.x / TX3) >> 1 == wrow) {
+        const float ccp = __ldg(P.c + (long long)s * L.field + L.off(z, y0 + en.x / TX3, x0 + en.x % TX3));
+        pl[en.x] += ccp * (__int_as_float(en.z) *
+                           P.series[(long long)b * P.series_bstride + (long long)t * P.series_ld + en.y]);
+      }
+      __syncwarp();
+      ie_cur += n;
+      inj_z = n < 32 ? __shfl_sync(0xffffffffu, en.w, n & 31) : z;
     }
-    ie_cur = e_end;
-    inj_z = ie_cur < ie_end ? P.inj[ie_cur].w : 0x7fffffff;
-    __syncwarp();
     const float4 v = ld4s(pl + ly * TX3 + lx);
     nv[0] = v.x; nv[1] = v.y; nv[2] = v.z; nv[3] = v.w;
-    int s_end = se_cur;
-    while (s_end < se_end && P.smp4[s_end].z == z) s_end++;
-    for (int e = se_cur + lane; e < s_end; e += 32) {
-      const int4 en = P.smp4[e];
-      if ((en.x / TX3) >> 1 != wrow) continue;
-      P.smp_out[(long long)b * P.smp_bstride_out + (long long)t * P.smp_ld + en.y] = pl[en.x];
+    while (smp_z == z) {
+      const int e = se_cur + lane;
+      int4 en = make_int4(0, 0, 0x7fffffff, 0);
+      if (e < se_end) en = P.smp4[e];
+      const bool here = en.z == z;
+      const int n = __popc(__ballot_sync(0xffffffffu, here));
+      if (here && (en.x / TX3) >> 1 == wrow)
+        P.smp_out[(long long)b * P.smp_bstride_out + (long long)t * P.smp_ld + en.y] = pl[en.x];
+      se_cur += n;
+      smp_z = n < 32 ? __shfl_sync(0xffffffffu, en.z, n & 31) : z;
     }
-    se_cur = s_end;
-    smp_z = se_cur < se_end ? P.smp4[se_cur].z : 0x7fffffff;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
 
