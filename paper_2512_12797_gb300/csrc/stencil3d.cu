@@ -792,14 +792,17 @@ cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMa
   }
   const long long cap = (long long)nsm * P.ctas_per_sm3;
   dim3 grid((unsigned)(P.ctas_per_sm3 > 0 && ncols > cap ? cap : ncols));
-  // The one-bracket form serves the forward only: on the layered 3D batch
-  // it made the forward step 4 % faster and the adjoint step (two
-  // Laplacians) 2 % slower.
-  if (adj)
-    return P.pair3 ? launch3<true, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
-                   : launch3<true, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
+  // On isotropic grids both recursions use the one-bracket Laplacian (the
+  // adjoint's imaging term has its own plain form, lap3_img).
   bool iso = true;
   for (int k = 1; k <= 4; k++) iso = iso && K.cx[k] == K.cy[k] && K.cx[k] == K.cz[k];
+  if (adj) {
+    if (P.pair3)
+      return iso ? launch3<true, true, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
+                 : launch3<true, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
+    return iso ? launch3<true, true, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
+               : launch3<true, false, false>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
+  }
   if (P.pair3)
     return iso ? launch3<false, true, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st)
                : launch3<false, false, true>(tm_halo, tm_plain, tm_cc, tm_g, L, K, Q, grid, st);
