@@ -312,7 +312,8 @@ int fwi_checkpoint_schedule(int nt, int64_t slots, int32_t* desc_out, int cap, i
  * minimises (chunks) x (2 nt + recomputed steps) x (time of one step launch). */
 int fwi_chunking(fwi_ctx* ctx, int* samples_per_chunk);
 
-/* Step-kernel variants.  2D: the TMA ring depth.  3D: variant bits
+/* Step-kernel variants.  2D: bit 0 the TMA ring depth, bit 1 the tile shape
+ * (128 x 32 or 128 x 24; the same arithmetic per point).  3D: variant bits
  *   bit 0  CTA order: all tiles of one wavefield back to back, or the tile of
  *          every wavefield of the launch side by side (a sample's supergathers
  *          then share its cc reads through L2);

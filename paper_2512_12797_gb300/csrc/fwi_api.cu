@@ -179,7 +179,7 @@ struct fwi_ctx {
   // receiver lists (shared by all wavefields): forward sampling, adjoint injection
   // per tile shape
   int* rec_off[2] = {};
-  int2* rec_smp = nullptr;      // 2D sampling entries
+  int2* rec_smp[2] = {};        // 2D sampling entries
   int4* rec_smp4[2] = {};       // 3D sampling entries (z in .z)
   int4* rec_inj[2] = {};        // adjoint injection entries (z in .w)
   // per-call lists
@@ -270,15 +270,16 @@ Coef make_coef(const fwi_grid* g) {
 inline int tile_rows3(int sh) { return sh ? TY3 / 2 : TY3; }
 
 // Tile of padded point (z, y, x) and its local index inside the tile.
-// 2D tiles are 128 (x) x 32 (z); 3D tiles are 64 (x) x 16 or 64 x 8 (y) columns in z.
+// 2D tiles are 128 (x) x 32 or 128 x 24 (z); 3D tiles are 64 (x) x 16 or 64 x 8 (y) columns in z.
 void tile_of(const fwi_ctx* C, const Entry& e, int sh, int* tile, int* local) {
   if (C->L.ndim == 3) {
     const int ty = tile_rows3(sh);
     *tile = (e.y / ty) * C->ntx + e.x / TX3;
     *local = (e.y % ty) * TX3 + (e.x % TX3);
   } else {
-    *tile = (e.z / TZ) * C->ntx + e.x / TX;
-    *local = (e.z % TZ) * TX + (e.x % TX);
+    const int tz = tile_rows2d(sh);
+    *tile = (e.z / tz) * C->ntx + e.x / TX;
+    *local = (e.z % tz) * TX + (e.x % TX);
   }
 }
 
@@ -333,18 +334,16 @@ int make_tmaps(fwi_ctx* C, int B, int nslots, Maps* M) {
   if (L.ndim == 2) {
     const cuuint64_t dims[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)B, (cuuint64_t)nslots};
     const cuuint64_t str[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.SX * L.NZ * 4, (cuuint64_t)L.field * B * 4};
-    const cuuint32_t bh[4] = {HX, HZ, 1, 1}, bp[4] = {TX, TZ, 1, 1};
     const cuuint64_t cd[3] = {(cuuint64_t)L.SX, (cuuint64_t)L.NZ, (cuuint64_t)C->max_B};
     const cuuint64_t cs[2] = {(cuuint64_t)L.SX * 4, (cuuint64_t)L.field * 4};
-    const cuuint32_t cb[3] = {TX, TZ, 1};
-    if (!encode(&M->th[0], 4, C->pool, dims, str, bh) || !encode(&M->tp[0], 4, C->pool, dims, str, bp) ||
-        !encode(&M->tc[0], 3, C->c, cd, cs, cb))
-      return FWI_ERR_CUDA;
-    M->tg[0] = M->tc[0];  // unused by the 2D kernels
-    M->th[1] = M->th[0];
-    M->tp[1] = M->tp[0];
-    M->tc[1] = M->tc[0];
-    M->tg[1] = M->tg[0];
+    for (int sh = 0; sh < 2; sh++) {
+      const cuuint32_t tz = (cuuint32_t)tile_rows2d(sh);
+      const cuuint32_t bh[4] = {HX, tz + 2 * HALO, 1, 1}, bp[4] = {TX, tz, 1, 1}, cb[3] = {TX, tz, 1};
+      if (!encode(&M->th[sh], 4, C->pool, dims, str, bh) || !encode(&M->tp[sh], 4, C->pool, dims, str, bp) ||
+          !encode(&M->tc[sh], 3, C->c, cd, cs, cb))
+        return FWI_ERR_CUDA;
+      M->tg[sh] = M->tc[sh];  // unused by the 2D kernels
+    }
     return FWI_OK;
   }
   const cuuint64_t dims[5] = {(cuuint64_t)L.SX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, (cuuint64_t)B,
@@ -424,7 +423,7 @@ int build_call_lists(fwi_ctx* C, int nsamp, const int32_t* perm, const int8_t* w
     p = (p + bytes + 255) / 256 * 256;
     return r;
   };
-  const int nsh = C->L.ndim == 3 ? 2 : 1;
+  const int nsh = 2;  // both tile shapes (3D: 64 x 16 and pairs; 2D: 128 x 32 and 128 x 24)
   for (int sh = 0; sh < 2; sh++) {
     const int sh_eff = sh < nsh ? sh : 0;  // 2D: shape 1 aliases shape 0
     if (sh != sh_eff) {
@@ -520,10 +519,15 @@ int validate_call(fwi_ctx* C, const float* vel, int nsamp, const int32_t* perm, 
 // tiles, for a sample with an even number of supergathers).  The autotuner
 // does not choose the adjoint's shape, since the pair form sums the imaging
 // term in another order and a timing-dependent choice would make results
-// depend on the run; 2D has one shape.
-int shape_fwd(const fwi_ctx* C) { return C->L.ndim == 3 ? (C->var[0] >> 2) & 1 : 0; }
+// depend on the run.  2D: variant bit 1 (128 x 32 or 128 x 24 tiles, the same
+// arithmetic per point), for the forward and the adjoint alike.
+int shape_fwd(const fwi_ctx* C) {
+  if (C->var[0] < 0) return 0;
+  return C->L.ndim == 3 ? (C->var[0] >> 2) & 1 : (C->var[0] >> 1) & 1;
+}
 int shape_adj(const fwi_ctx* C, int nsg) {
-  return C->L.ndim == 3 && nsg % 2 == 0 && C->var[1] >= 0 && (C->var[1] & 4) ? 1 : 0;
+  if (C->L.ndim == 2) return C->var[1] >= 0 ? (C->var[1] >> 1) & 1 : 0;
+  return nsg % 2 == 0 && C->var[1] >= 0 && (C->var[1] & 4) ? 1 : 0;
 }
 
 StepParams base_params(fwi_ctx* C, int B, int nsg, int sh = 0) {
@@ -582,8 +586,8 @@ int run_steps(fwi_ctx* C, bool adj, StepParams P, int off, int n, int nsamp, int
   P.steps = C->desc + off;
   P.nsteps = n;
   P.done = C->done;
-  CK(cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st));
-  CK(launch_step2d(adj, C->var[adj ? 1 : 0], M.th[0], M.tp[0], M.tc[0], C->L, C->K, P, nsamp, st));
+  CK(cudaMemsetAsync(C->done, 0, (size_t)nsamp * P.ntiles * 4, st));
+  CK(launch_step2d(adj, C->var[adj ? 1 : 0], M.th[sh], M.tp[sh], M.tc[sh], C->L, C->K, P, nsamp, st));
   *launches += 1;
   return FWI_OK;
 }
@@ -664,9 +668,9 @@ cudaError_t launch_tune(fwi_ctx* C, bool adj, int v, StepParams P, const StepDes
     }
     return cudaSuccess;
   }
-  cudaError_t e = cudaMemsetAsync(C->done, 0, (size_t)nsamp * C->ntiles * 4, st);
+  cudaError_t e = cudaMemsetAsync(C->done, 0, (size_t)nsamp * P.ntiles * 4, st);
   if (e != cudaSuccess) return e;
-  return launch_step2d(adj, v, M.th[0], M.tp[0], M.tc[0], C->L, C->K, P, nsamp, st);
+  return launch_step2d(adj, v, M.th[P.pair3], M.tp[P.pair3], M.tc[P.pair3], C->L, C->K, P, nsamp, st);
 }
 
 // Autotuner: time every variant of the forward and adjoint step kernels on
@@ -709,8 +713,8 @@ int autotune(fwi_ctx* C, int nsamp, int nsg, const Maps& M, long long nslots, cu
       if (C->L.ndim == 3 && adj && (v & 4)) continue;  // the adjoint's tile shape is not tuned (shape_adj)
       if (C->L.ndim == 3 && (v & 16) && !(v & 8)) continue;  // multi-step needs the persistent grid
       // pair tiles need an even number of supergathers per sample
-      const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : 0;
-      if (sh && nsg % 2) continue;
+      const int sh = C->L.ndim == 3 ? (adj ? shape_adj(C, nsg) : (v >> 2) & 1) : (v >> 1) & 1;
+      if (C->L.ndim == 3 && sh && nsg % 2) continue;
       StepParams P = base_params(C, B, nsg, sh);
       P.inj_off = C->zero_off;
       P.inj_bstride = 0;
@@ -830,7 +834,8 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
   C->nty = (L.nyp + TY3 - 1) / TY3;
   C->ntiles = C->ntx * (g->ndim == 3 ? C->nty : C->ntz);
   C->ntiles_s[0] = C->ntiles;
-  C->ntiles_s[1] = g->ndim == 3 ? C->ntx * ((L.nyp + tile_rows3(1) - 1) / tile_rows3(1)) : 0;
+  C->ntiles_s[1] = g->ndim == 3 ? C->ntx * ((L.nyp + tile_rows3(1) - 1) / tile_rows3(1))
+                                 : C->ntx * ((L.nzp + tile_rows2d(1) - 1) / tile_rows2d(1));
   C->Emax = std::min(C->ns, 4096);
   C->nblk = 64;
 
@@ -847,7 +852,7 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
     return FWI_ERR_OOM;
   }
   // receiver lists, shared by every wavefield, per tile shape
-  for (int sh = 0; sh < (g->ndim == 3 ? 2 : 1); sh++) {
+  for (int sh = 0; sh < 2; sh++) {
     std::vector<std::vector<Entry>> rl(1);
     for (int r = 0; r < C->nr; r++) rl[0].push_back({C->rec_zyx[3 * r], C->rec_zyx[3 * r + 1], C->rec_zyx[3 * r + 2], r, 1.f});
     std::vector<int> off(C->ntiles_s[sh] + 1);
@@ -865,23 +870,18 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
       v.w = e.z;
       inj[pos] = v;
     });
-    if (!alloc((void**)&C->rec_off[sh], off.size() * 4) || (sh == 0 && !alloc((void**)&C->rec_smp, smp.size() * 8)) ||
+    if (!alloc((void**)&C->rec_off[sh], off.size() * 4) || (g->ndim == 2 && !alloc((void**)&C->rec_smp[sh], smp.size() * 8)) ||
         !alloc((void**)&C->rec_smp4[sh], smp4.size() * 16) || !alloc((void**)&C->rec_inj[sh], inj.size() * 16)) {
       fwi_destroy(C);
       return FWI_ERR_OOM;
     }
     if (cudaMemcpy(C->rec_off[sh], off.data(), off.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (sh == 0 && cudaMemcpy(C->rec_smp, smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (g->ndim == 2 && cudaMemcpy(C->rec_smp[sh], smp.data(), smp.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(C->rec_smp4[sh], smp4.data(), smp4.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(C->rec_inj[sh], inj.data(), inj.size() * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
       fwi_destroy(C);
       return FWI_ERR_CUDA;
     }
-  }
-  if (g->ndim == 2) {  // one tile shape: shape 1 aliases shape 0
-    C->rec_off[1] = C->rec_off[0];
-    C->rec_smp4[1] = C->rec_smp4[0];
-    C->rec_inj[1] = C->rec_inj[0];
   }
   const int ntiles_max = std::max(C->ntiles_s[0], C->ntiles_s[1]);
   if (!alloc((void**)&C->zero_off, (size_t)(ntiles_max + 1) * 4) ||
@@ -944,7 +944,7 @@ int fwi_create(const fwi_grid* g, const fwi_geom* geom, int max_wavefields, size
         return false;
       }() ||
       !alloc((void**)&C->tdesc, kTuneSteps * sizeof(StepDesc)) ||
-      !alloc((void**)&C->done, (size_t)B * C->ntiles * 4)) {
+      !alloc((void**)&C->done, (size_t)B * std::max(C->ntiles_s[0], C->ntiles_s[1]) * 4)) {
     fwi_destroy(C);
     return FWI_ERR_OOM;
   }
@@ -989,12 +989,13 @@ void fwi_destroy(fwi_ctx* C) {
   cudaFree(C->qsrc);
   cudaFree(C->stmp);
   cudaFree(C->status);
-  for (int sh = 0; sh < (C->L.ndim == 3 ? 2 : 1); sh++) {
+  for (int sh = 0; sh < 2; sh++) {
     cudaFree(C->rec_off[sh]);
     cudaFree(C->rec_smp4[sh]);
     cudaFree(C->rec_inj[sh]);
   }
-  cudaFree(C->rec_smp);
+  cudaFree(C->rec_smp[0]);
+  cudaFree(C->rec_smp[1]);
   cudaFree(C->dlist);
   cudaFree(C->zero_off);
   cudaFree(C->gtab);
@@ -1062,7 +1063,7 @@ static int run_forward_loop(fwi_ctx* C, int nsamp, int nsg, const CallLists& cl,
   if (C->L.ndim == 3)
     P.smp4 = C->rec_smp4[sh];
   else
-    P.smp = C->rec_smp;
+    P.smp = C->rec_smp[sh];
   P.smp_out = dout;
   P.smp_bstride_out = (long long)C->g.nt * C->nr;
   P.smp_ld = C->nr;

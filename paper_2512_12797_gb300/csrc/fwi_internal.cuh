@@ -97,6 +97,8 @@ cudaError_t launch_step2d(bool adj, int variant, const CUtensorMap& tm_halo, con
                           const CUtensorMap& tm_c, const Layout& L, const Coef& K, const StepParams& P, int nsamp,
                           cudaStream_t st);
 int num_variants2d(bool adj);
+// Rows of a 2D tile for tile shape sh (variant bit 1): 128 x 32, or 128 x 24.
+int tile_rows2d(int sh);
 const char* variant2d_name(bool adj, int v);
 cudaError_t launch_step3d(bool adj, const CUtensorMap& tm_halo, const CUtensorMap& tm_plain,
                           const CUtensorMap& tm_cc, const CUtensorMap& tm_g, const Layout& L, const Coef& K,

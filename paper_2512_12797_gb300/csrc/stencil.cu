@@ -45,8 +45,8 @@
 
 namespace fwi {
 
-constexpr int R2D = 4;                       // rows per consumer thread
-constexpr int NCW2D = TZ / R2D;              // consumer warps (8)
+constexpr int NCW2D = 8;                     // consumer warps; R rows per thread, tiles of 8R rows
+__host__ __device__ constexpr int tile_rows2(int R) { return NCW2D * R; }
 constexpr int NTHREADS2D = 32 * NCW2D + 128;  // + producer warpgroup
 constexpr int PCAP = 128;                    // point-list entries staged per stage and list
 constexpr int WDONE = 8;                     // item-completion counters (ring)
@@ -66,10 +66,10 @@ constexpr bool kL2Hints = true;
 //   PTS[32 ..]  = injection local index [PCAP], injection value [PCAP],
 //                 sampling local index [PCAP], sampling record column [PCAP].
 // Two cc tiles follow the stages.  Every part starts on 128 bytes.
-template <bool ADJ, int NS>
+template <bool ADJ, int NS, int R>
 struct Smem2D {
-  static constexpr int IN = HZ * HX;   // floats in one halo tile
-  static constexpr int PV = TZ * TX;   // floats in one plain tile
+  static constexpr int IN = (tile_rows2(R) + 2 * HALO) * HX;  // floats in one halo tile
+  static constexpr int PV = tile_rows2(R) * TX;               // floats in one plain tile
   static constexpr int PTS = 32 + 4 * PCAP;
   static constexpr int OFF_SNAP = IN + PV;
   static constexpr int OFF_PTS = OFF_SNAP + (ADJ ? IN : 0);
@@ -236,12 +236,12 @@ __device__ __forceinline__ void drain(uint64_t* bars, int nbars, int issued, int
 
 // Warp 8, lane 0: TMA ring.  Iteration m = ((step n, item k), supergather j)
 // fills stage m % NS; the cc tile of (n, k) goes to buffer ic & 1.
-template <bool ADJ, int NS>
+template <bool ADJ, int NS, int R>
 __device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CUtensorMap* tm_plain,
                                             const CUtensorMap* tm_c, const StepParams& P, float* sm,
                                             uint64_t* full, uint64_t* empty, uint64_t* cfull, uint64_t* cempty,
                                             int* deps_ok, int my_items, volatile int* abort_flag) {
-  using S = Smem2D<ADJ, NS>;
+  using S = Smem2D<ADJ, NS, R>;
   constexpr uint32_t TX_BYTES = (S::IN + S::PV + (ADJ ? S::IN : 0)) * 4;
   const int G = gridDim.x, nsg = P.nsg;
   const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
@@ -251,7 +251,7 @@ __device__ __forceinline__ void produce_tma(const CUtensorMap* tm_halo, const CU
     for (int k = 0; k < my_items; k++, ic++) {
       const int item = (int)blockIdx.x + k * G;
       const int s = item / P.ntiles, tile = item - s * P.ntiles;
-      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * tile_rows2(R);
       if (n > 0) {  // neighbourhood of (n, k) ready: counted by warp 11
         const long long t0 = clock64();
         while (ld_acquire_cta_shared(deps_ok) <= ic) {
@@ -302,11 +302,11 @@ aborted:
 // sampling entries into the stage's PTS block (at most PCAP of each; the
 // consumers take any rest from global memory), then arrives on the stage's
 // full barrier.  Offsets of an item's supergathers are loaded one item ahead.
-template <bool ADJ, int NS>
+template <bool ADJ, int NS, int R>
 __device__ __forceinline__ void produce_points(const Layout& L, const StepParams& P, float* sm, uint64_t* full,
                                                uint64_t* empty, int my_items, int lane,
                                                volatile int* abort_flag) {
-  using S = Smem2D<ADJ, NS>;
+  using S = Smem2D<ADJ, NS, R>;
   const int G = gridDim.x, nsg = P.nsg;
   const bool has_smp = P.smp != nullptr;
   // offsets of supergather j0 + lane of item k: inj [a0, a1), smp [b0, b1)
@@ -334,7 +334,7 @@ __device__ __forceinline__ void produce_points(const Layout& L, const StepParams
     for (int k = 0; k < my_items; k++) {
       const int item = (int)blockIdx.x + k * G;
       const int s = item / P.ntiles, tile = item - s * P.ntiles;
-      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * tile_rows2(R);
       const float* cs = P.c + (long long)s * L.field;
       for (int j0 = 0; j0 < nsg; j0 += 32) {
         int a0 = na0, a1 = na1, b0 = nb0, b1 = nb1;
@@ -443,13 +443,13 @@ __device__ __forceinline__ void publish(const StepParams& P, int* wdone, int my_
   }
 }
 
-template <bool ADJ, int NS, bool ISO>
+template <bool ADJ, int NS, bool ISO, int R>
 __global__ void __launch_bounds__(NTHREADS2D, 1)
 step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant__ CUtensorMap tm_plain,
               const __grid_constant__ CUtensorMap tm_c, const Layout L, const Coef K, const StepParams P,
               int nitems) {
-  using S = Smem2D<ADJ, NS>;
-  constexpr int R = R2D, NCW = NCW2D;
+  using S = Smem2D<ADJ, NS, R>;
+  constexpr int NCW = NCW2D, TZR = tile_rows2(R);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + S::nfloat * 4);
@@ -488,10 +488,10 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   if (warp >= NCW) {  // ------------------------------------------- producer warpgroup
     setmaxnreg_dec<REG_PRODUCER>();
     if (warp == NCW && lane == 0)
-      produce_tma<ADJ, NS>(&tm_halo, &tm_plain, &tm_c, P, sm, full, empty, cfull, cempty, deps_ok, my_items,
+      produce_tma<ADJ, NS, R>(&tm_halo, &tm_plain, &tm_c, P, sm, full, empty, cfull, cempty, deps_ok, my_items,
                            abort_flag);
     else if (warp == NCW + 1)
-      produce_points<ADJ, NS>(L, P, sm, full, empty, my_items, lane, abort_flag);
+      produce_points<ADJ, NS, R>(L, P, sm, full, empty, my_items, lane, abort_flag);
     else if (warp == NCW + 2 && lane == 0)
       publish(P, wdone, my_items, abort_flag);
     else if (warp == NCW + 3 && lane == 0)
@@ -511,7 +511,7 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
   auto prefetch_item = [&](int k_) {
     const int item_ = (int)blockIdx.x + k_ * G;
     const int s_ = item_ / P.ntiles, tile_ = item_ - s_ * P.ntiles;
-    const int gx_ = (tile_ % P.ntx) * TX + lx, zb = (tile_ / P.ntx) * TZ + lz;
+    const int gx_ = (tile_ % P.ntx) * TX + lx, zb = (tile_ / P.ntx) * TZR + lz;
 #pragma unroll
     for (int r = 0; r < R; r++) {
       const bool v = zb + r < L.nzp && gx_ < L.nxp;
@@ -540,11 +540,11 @@ step2d_kernel(const __grid_constant__ CUtensorMap tm_halo, const __grid_constant
     for (int k = 0; k < my_items; k++, ic++) {
       const int item = (int)blockIdx.x + k * G;
       const int s = item / P.ntiles, tile = item - s * P.ntiles;
-      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZ;
+      const int x0 = (tile % P.ntx) * TX, z0 = (tile / P.ntx) * TZR;
       const int gx = x0 + lx;
       const bool colv0 = gx < L.nxp, live = z0 + lz < L.nzp;
       const bool sponge =
-          L.nb > 0 && (x0 < L.nb || x0 + TX > L.nb + L.nx || z0 < L.nb || z0 + TZ > L.nb + L.nz);
+          L.nb > 0 && (x0 < L.nb || x0 + TX > L.nb + L.nx || z0 < L.nb || z0 + TZR > L.nb + L.nz);
       bool rowv[R];
       float cc[R][4], bc[R][4];
 #pragma unroll
@@ -736,18 +736,18 @@ static int num_sms() {
   return n;
 }
 
-// Compiled variants differ in the ring depth NS only; the arithmetic per grid
-// point is the same in every variant, so their results are bit-identical and
-// the autotuner in fwi_api.cu picks the fastest per call shape.  The launch is
+// Compiled variants differ in the ring depth NS and the tile height (8R rows:
+// 128 x 32 or 128 x 24); the arithmetic per grid point is the same in every
+// variant, so their results are bit-identical and the autotuner in fwi_api.cu picks the fastest per call shape.  The launch is
 // cooperative: CTAs wait on one another's progress flags, so all of them must
 // be resident (one per SM).
-template <bool ADJ, int NS, bool ISO>
+template <bool ADJ, int NS, bool ISO, int R>
 static cudaError_t launch_iso(const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc, const Layout& L,
                               const Coef& K, const StepParams& P, int nsamp, cudaStream_t st) {
-  using S = Smem2D<ADJ, NS>;
+  using S = Smem2D<ADJ, NS, R>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ADJ, NS, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(step2d_kernel<ADJ, NS, ISO, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          S::bytes);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -763,15 +763,15 @@ static cudaError_t launch_iso(const CUtensorMap& th, const CUtensorMap& tp, cons
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, step2d_kernel<ADJ, NS, ISO>, th, tp, tc, L, K, P, nitems);
+  return cudaLaunchKernelEx(&cfg, step2d_kernel<ADJ, NS, ISO, R>, th, tp, tc, L, K, P, nitems);
 }
 
-template <bool ADJ, int NS>
+template <bool ADJ, int NS, int R>
 static cudaError_t launch_variant(const CUtensorMap& th, const CUtensorMap& tp, const CUtensorMap& tc,
                                   const Layout& L, const Coef& K, const StepParams& P, int nsamp, cudaStream_t st) {
   if (K.cx[1] == K.cz[1] && K.cx[2] == K.cz[2] && K.cx[3] == K.cz[3] && K.cx[4] == K.cz[4])
-    return launch_iso<ADJ, NS, true>(th, tp, tc, L, K, P, nsamp, st);
-  return launch_iso<ADJ, NS, false>(th, tp, tc, L, K, P, nsamp, st);
+    return launch_iso<ADJ, NS, true, R>(th, tp, tc, L, K, P, nsamp, st);
+  return launch_iso<ADJ, NS, false, R>(th, tp, tc, L, K, P, nsamp, st);
 }
 
 struct Variant2D {
@@ -780,14 +780,21 @@ struct Variant2D {
                     const StepParams&, int, cudaStream_t);
 };
 
+// Variant v: bit 0 the ring depth, bit 1 the tile shape (tile_shape2d).
 static const Variant2D kFwd2D[] = {
-    {"fwd2d NS4 (8+4 warps)", launch_variant<false, 4>},
-    {"fwd2d NS3 (8+4 warps)", launch_variant<false, 3>},
+    {"fwd2d 128x32 NS4 (8+4 warps)", launch_variant<false, 4, 4>},
+    {"fwd2d 128x32 NS3 (8+4 warps)", launch_variant<false, 3, 4>},
+    {"fwd2d 128x24 NS4 (8+4 warps)", launch_variant<false, 4, 3>},
+    {"fwd2d 128x24 NS3 (8+4 warps)", launch_variant<false, 3, 3>},
 };
 static const Variant2D kAdj2D[] = {
-    {"adj2d NS3 (8+4 warps)", launch_variant<true, 3>},
-    {"adj2d NS2 (8+4 warps)", launch_variant<true, 2>},
+    {"adj2d 128x32 NS3 (8+4 warps)", launch_variant<true, 3, 4>},
+    {"adj2d 128x32 NS2 (8+4 warps)", launch_variant<true, 2, 4>},
+    {"adj2d 128x24 NS3 (8+4 warps)", launch_variant<true, 3, 3>},
+    {"adj2d 128x24 NS2 (8+4 warps)", launch_variant<true, 2, 3>},
 };
+
+int tile_rows2d(int sh) { return sh ? tile_rows2(3) : tile_rows2(4); }
 
 int num_variants2d(bool adj) {
   return adj ? (int)(sizeof(kAdj2D) / sizeof(kAdj2D[0])) : (int)(sizeof(kFwd2D) / sizeof(kFwd2D[0]));
