@@ -205,21 +205,32 @@ def reference_arm(args):
     return 0
 
 
+def kernel_source_hash(src_name, root=None):
+    """sha256 of a CUDA source with its comments and blank lines removed: the
+    key of an ncu figure taken on that source, unchanged by edits to comments."""
+    import hashlib
+    import re
+    src = open(os.path.join(root or ROOT, "paper_2512_12797_gb300", "csrc", src_name)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()
+
+
 def committed_traffic(kernel_name, ndim):
     """DRAM bytes per wavefield point update of the named step kernel from the
-    committed ncu summary, if it was taken on the current kernel source (else None)."""
-    import hashlib
+    committed ncu summary, if it was taken on the current kernel code (else None)."""
     import re
     src_name = "stencil3d.cu" if ndim == 3 else "stencil.cu"
     prof = "step3d_layered3d_traffic.md" if ndim == 3 else "step2d_thrust2d_traffic.md"
     try:
-        src = open(os.path.join(ROOT, "paper_2512_12797_gb300", "csrc", src_name), "rb").read()
+        key = kernel_source_hash(src_name)
         txt = open(os.path.join(ROOT, "profiles", prof)).read()
     except OSError:
         return None
-    m = re.search(r"traffic-key %s sha256=([0-9a-f]+) forward_bytes_per_update=([0-9.]+) "
+    m = re.search(r"traffic-key %s code-sha256=([0-9a-f]+) forward_bytes_per_update=([0-9.]+) "
                   r"adjoint_bytes_per_update=([0-9.]+)" % re.escape(src_name), txt)
-    if not m or m.group(1) != hashlib.sha256(src).hexdigest():
+    if not m or m.group(1) != key:
         return None
     return float(m.group(3) if "ADJ" in kernel_name else m.group(2))
 

@@ -31,10 +31,10 @@
 // memory (the second wavefield's warp hands its q L p to the first's, through
 // a two-buffer exchange guarded by mbarriers) and go into one accumulator per
 // pair: G += q_a L p_a + q_b L p_b.  The forward's arithmetic per point is
-// the same in both tile forms; the adjoint's accumulator sums in another order
-// than the per-wavefield form, so the library picks the adjoint's form by
-// rule (pairs whenever a sample has an even number of supergathers), not by
-// timing.
+// the same in both tile forms, so the autotuner may pick either; the
+// adjoint's accumulator sums in another order than the per-wavefield form, so
+// the pair adjoint is never chosen by timing: it runs only when a forced
+// variant selects it.
 #include "fwi_internal.cuh"
 
 namespace fwi {

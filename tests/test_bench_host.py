@@ -25,7 +25,7 @@ def _key(ndim):
     src = "stencil3d.cu" if ndim == 3 else "stencil.cu"
     prof = "step3d_layered3d_traffic.md" if ndim == 3 else "step2d_thrust2d_traffic.md"
     txt = open(os.path.join(bench.ROOT, "profiles", prof)).read()
-    m = re.search(r"traffic-key %s sha256=([0-9a-f]+) forward_bytes_per_update=([0-9.]+) "
+    m = re.search(r"traffic-key %s code-sha256=([0-9a-f]+) forward_bytes_per_update=([0-9.]+) "
                   r"adjoint_bytes_per_update=([0-9.]+)" % re.escape(src), txt)
     assert m, prof
     return src, m
@@ -35,8 +35,7 @@ def test_committed_traffic_follows_the_kernel_source():
     for ndim in (2, 3):
         src, m = _key(ndim)
         kd = "3d" if ndim == 3 else "2d"
-        cur = hashlib.sha256(open(os.path.join(bench.ROOT, "paper_2512_12797_gb300", "csrc", src), "rb")
-                             .read()).hexdigest()
+        cur = bench.kernel_source_hash(src)
         fwd = bench.committed_traffic("step%s_kernel<FWD>" % kd, ndim)
         adj = bench.committed_traffic("step%s_kernel<ADJ>" % kd, ndim)
         if cur == m.group(1):
@@ -48,14 +47,23 @@ def test_committed_traffic_follows_the_kernel_source():
             assert fwd is None and adj is None
 
 
+def test_kernel_hash_ignores_comments_only():
+    src = open(os.path.join(bench.ROOT, "paper_2512_12797_gb300", "csrc", "stencil3d.cu")).read()
+    assert "//" in src
+    h = hashlib.sha256(src.encode()).hexdigest()
+    assert bench.kernel_source_hash("stencil3d.cu") != h  # not the file's own hash
+
+
 def test_stale_traffic_is_null(tmp_path, monkeypatch):
-    # a copy of the tree whose kernel source differs by one byte
+    # a copy of the tree whose kernel code differs by one statement, and one
+    # whose comments differ
     for d in ("profiles", os.path.join("paper_2512_12797_gb300", "csrc")):
         os.makedirs(tmp_path / d, exist_ok=True)
     shutil.copy(os.path.join(bench.ROOT, "profiles", "step3d_layered3d_traffic.md"), tmp_path / "profiles")
     src = open(os.path.join(bench.ROOT, "paper_2512_12797_gb300", "csrc", "stencil3d.cu"), "rb").read()
-    (tmp_path / "paper_2512_12797_gb300" / "csrc" / "stencil3d.cu").write_bytes(src + b"\n")
+    out = tmp_path / "paper_2512_12797_gb300" / "csrc" / "stencil3d.cu"
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    out.write_bytes(src + b"\nstatic int changed_code;\n")
     assert bench.committed_traffic("step3d_kernel<FWD>", 3) is None
-    (tmp_path / "paper_2512_12797_gb300" / "csrc" / "stencil3d.cu").write_bytes(src)
+    out.write_bytes(src + b"\n// a comment\n\n")
     assert bench.committed_traffic("step3d_kernel<FWD>", 3) == float(_key(3)[1].group(2))
